@@ -1,0 +1,124 @@
+"""Seeded synthetic inputs for the BZ front-propagation workloads.
+
+This module only generates input data (initial states on the finest grid and
+random instance parameters).  It holds none of the method's arithmetic and is
+the one piece of code that both the GPU path's callers and the oracle's tests
+use.  The paper prints no initial data (Sec. 4 shows BZ fronts, Fig. 3), so
+the recipes below are the ones stated in the design notes:
+
+* a tanh front of width w in b = u2 between the rest state b_r and an excited
+  value b_e, c = u3 = b, and a = u1 slaved to the fast manifold a = f c/(q + b);
+* "1% seeded noise": a multiplicative factor (1 + 0.01 xi), xi ~ U[-1, 1];
+* "smooth seeded noise": the front position is perturbed by 8 seeded Fourier
+  modes of amplitude 0.01 (so the details stay small away from the front).
+
+Random numbers come from splitmix64(seed XOR index) mapped to [0, 1).
+Cell values are point values at cell centres of the finest level J, laid out
+as an array of shape (m, 2^(d J)) with x fastest (lexicographic).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BZ_DEFAULT = dict(eps=1e-2, mu=1e-5, f=1.6, q=2e-3)
+BZ_D = (2.5e-3, 2.5e-3, 1.5e-3)
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser applied elementwise to uint64 inputs (Steele et al.)."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, index: np.ndarray) -> np.ndarray:
+    """U[0,1) doubles from splitmix64(seed ^ index), 53 significant bits."""
+    z = splitmix64(np.uint64(seed) ^ np.asarray(index, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def bz_rest_state(f: float, q: float) -> float:
+    """Positive root b of b^2 + (q + f - 1) b - q (1 + f) = 0 (the BZ fixed point)."""
+    bq = q + f - 1.0
+    return 0.5 * (-bq + np.sqrt(bq * bq + 4.0 * q * (1.0 + f)))
+
+
+def cell_centres(d: int, J: int):
+    n = 1 << J
+    x = (np.arange(n) + 0.5) / n
+    grids = np.meshgrid(*([x] * d), indexing="ij")
+    # lexicographic with x fastest: coordinate a varies with stride n^a
+    return [g.transpose(tuple(range(d))[::-1]).ravel() for g in grids]
+
+
+def _profile(s, w):
+    return 0.5 * (1.0 - np.tanh(s / w))
+
+
+def _fourier(seed: int, t: np.ndarray, nmodes: int = 8, amp: float = 0.01) -> np.ndarray:
+    r = uniform(seed, np.arange(2 * nmodes, dtype=np.uint64))
+    out = np.zeros_like(t)
+    for k in range(nmodes):
+        out += np.sin(2.0 * np.pi * (k + 1) * t + 2.0 * np.pi * r[2 * k]) * (r[2 * k + 1] - 0.5)
+    return amp * out / (0.5 * nmodes ** 0.5)
+
+
+def bz_state(b: np.ndarray, c: np.ndarray, f: float, q: float) -> np.ndarray:
+    a = f * c / (q + b)
+    return np.stack([a, b, c])
+
+
+def bz_front_2d(J: int, seed: int, x0: float = 0.5, w: float = 0.02, noise: float = 0.01,
+                f: float = BZ_DEFAULT["f"], q: float = BZ_DEFAULT["q"], be: float = 0.8):
+    """2D front in x at x0 with multiplicative white noise (uniform 128x128 workload)."""
+    x, y = cell_centres(2, J)
+    br = bz_rest_state(f, q)
+    b = br + (be - br) * _profile(x - x0, w)
+    u = bz_state(b, b.copy(), f, q)
+    if noise:
+        idx = np.arange(u.size, dtype=np.uint64)
+        xi = 2.0 * uniform(seed, idx) - 1.0
+        u = u * (1.0 + noise * xi.reshape(u.shape))
+    return u
+
+
+def bz_cross_2d(J: int, seed: int, w: float = 0.02, f: float = BZ_DEFAULT["f"],
+                q: float = BZ_DEFAULT["q"], be: float = 0.8, x0: float = 0.5, y0: float = 0.5):
+    """Two crossing fronts: b from a front along x = x0(y), c from a front along y = y0(x),
+    both positions perturbed by smooth seeded Fourier noise."""
+    x, y = cell_centres(2, J)
+    br = bz_rest_state(f, q)
+    px = x0 + _fourier(seed, y)
+    py = y0 + _fourier(seed + 1, x)
+    b = br + (be - br) * _profile(x - px, w)
+    c = br + (be - br) * _profile(y - py, w)
+    return bz_state(b, c, f, q)
+
+
+def bz_sphere_3d(J: int, seed: int, r0: float = 0.3, w: float = 0.02,
+                 f: float = BZ_DEFAULT["f"], q: float = BZ_DEFAULT["q"], be: float = 0.8):
+    """Spherical front of radius r0 about the centre, radius perturbed smoothly."""
+    x, y, z = cell_centres(3, J)
+    br = bz_rest_state(f, q)
+    dx, dy, dz = x - 0.5, y - 0.5, z - 0.5
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    th = np.arctan2(dy, dx) / (2.0 * np.pi)
+    ph = np.arccos(np.clip(dz / np.maximum(r, 1e-300), -1.0, 1.0)) / np.pi
+    rr = r0 + 0.5 * (_fourier(seed, th) + _fourier(seed + 1, ph))
+    b = br + (be - br) * _profile(r - rr, w)
+    return bz_state(b, b.copy(), f, q)
+
+
+def batch_instances(n: int, master_seed: int = 2026):
+    """Per-instance parameters of the batched workload: J ~ U{7..10}, f ~ U[0.9, 2.0],
+    eta log-uniform in [1e-4, 1e-2], front position ~ U[0.2, 0.8]."""
+    out = []
+    for i in range(n):
+        s = int(splitmix64(np.uint64(master_seed) ^ np.uint64(i)))
+        r = uniform(s, np.arange(4, dtype=np.uint64))
+        out.append(dict(seed=s, J=7 + int(r[0] * 4), f=0.9 + 1.1 * r[1],
+                        eta=10.0 ** (-4.0 + 2.0 * r[2]), x0=0.2 + 0.6 * r[3]))
+    return out
