@@ -1,0 +1,171 @@
+/*
+ * mr.h -- C-ABI of the GB300 (sm_103a) library for the adaptive-multiresolution
+ * Strang step of Descombes, Duarte, Dumont, Guillet, Louvet, Massot,
+ * "Task-based adaptive multiresolution for time-space multi-scale
+ * reaction-diffusion systems on multi-core architectures" (arXiv:1506.04651).
+ *
+ * The library advances du_i/dt - div(D_i grad u_i) = f_i(u) on [0,1]^d with
+ * homogeneous Neumann conditions (Sec. 1, Eq. thesystem) by the Strang scheme
+ * U_{n+1} = R_{dt/2} D_dt R_{dt/2} U_n (Sec. 2.1) on the leaves of a graded
+ * dyadic tree adapted every step by multiresolution (Sec. 2.2, Sec. 3.1).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns mr_status; nothing throws across the ABI.
+ *   - Pointers are plain host or device pointers; an `on_device` flag (0 host,
+ *     1 device) says which.  The caller owns every buffer it passes; the
+ *     context owns all device memory it allocates (freed by mr_destroy).
+ *   - Work is ordered on the CUDA stream given to mr_create (0 = legacy
+ *     default stream).  Calls synchronise that stream before returning.
+ *   - Leaf order: by level, then by Morton abscissa within a level (the key
+ *     order below).  Leaf values are structure-of-arrays: values[i*n + r] is
+ *     species i of leaf r (Sec. 3.2: one contiguous array per unknown).
+ *   - Keys follow Sec. 3.1.1 / Fig. 2: bits 0-47 the Morton abscissa of the
+ *     cell at its level (x digit first in each digit group), bits 48-51 the
+ *     level, bits 52-63 zero.
+ *   - Errors: MR_EINVAL for bad arguments (checked before any GPU work),
+ *     MR_ENOMEM when a capacity is exceeded, MR_ECUDA for a CUDA runtime
+ *     error, per-cell Radau5 failures as MR_ERADAU_* (first one wins; the
+ *     leaf values are then those reached when the failing cell stopped).
+ *     mr_last_error() gives a one-line message.
+ */
+#ifndef MR_GB300_H
+#define MR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mr_ctx mr_ctx;
+
+typedef enum {
+  MR_OK = 0,
+  MR_EINVAL = -1,
+  MR_ENOMEM = -2,
+  MR_ECUDA = -3,
+  MR_ESTATE = -4,
+  MR_ERADAU_HMIN = -10,
+  MR_ERADAU_MAXSTEPS = -11,
+  MR_ERADAU_SINGULAR = -12,
+  MR_EROCK_STEP = -20,
+  MR_ENONFINITE = -30,
+  MR_ETIMEOUT = -40
+} mr_status;
+
+enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2 };
+enum { MR_FP64 = 0, MR_MIXED = 1 };
+
+#define MR_MAX_SPECIES 16
+#define MR_MAX_LEVEL 16
+
+/*
+ * Problem description (Sec. 1, Eq. thesystem).
+ *   dim       d in {2, 3}
+ *   J         finest level (Sec. 2.2); d*J <= 30
+ *   jmin      no leaf is coarser than jmin (1 <= jmin <= J)
+ *   m         number of species (BZ: 3, NAGUMO: 1)
+ *   model     MR_MODEL_BZ: params = (eps, mu, f, q) of
+ *               f_a = (-q a - a b + f c)/mu, f_b = (b - b^2 + a (q - b))/eps, f_c = b - c
+ *               (Sec. 1 item II; the paper prints q = 0.02)
+ *             MR_MODEL_NAGUMO: params = (k) of f = k u^2 (1 - u) (Sec. 1 item I)
+ *   D         m diffusion coefficients
+ *   precision MR_FP64 (the only form built so far)
+ *   max_leaves leaf capacity; 0 means 2^(d J)
+ */
+typedef struct {
+  int dim, J, jmin, m, model, nparams, precision, reserved;
+  double params[8];
+  double D[MR_MAX_SPECIES];
+  int64_t max_leaves;
+} mr_problem;
+
+/* Counters of the last completed calls (see each field). */
+typedef struct {
+  int64_t leaves, nodes;
+  int64_t leaves_per_level[MR_MAX_LEVEL + 1];
+  double compression_ratio;       /* CR = (1 - N/2^(dJ)) 100, Sec. 4.1 */
+  /* last react_radau5 call (App. A complexity: fev + m * jac) */
+  int64_t radau_fev, radau_jac, radau_steps, radau_accept, radau_reject, radau_newton, radau_dec;
+  /* last diffuse_rock4 call, summed over species */
+  int64_t rock_steps, rock_reject, rock_stages, rock_matvec;
+  int32_t rock_smax, reserved0;
+  double rock_rho;                /* Gershgorin bound of the species-free operator */
+  int64_t irregular_rows, irregular_nnz;
+  double ms_adapt, ms_react, ms_diffuse; /* device time of the last strang_step phases */
+  int64_t kernel_launches;        /* cumulative kernels launched by this context */
+} mr_stats;
+
+/* Create a context for `prob` on `cuda_stream` (a cudaStream_t or NULL).
+ * Allocates the device capacity for the full tree once.  MR_EINVAL on bad
+ * sizes, MR_ENOMEM if the device cannot hold the capacity. */
+mr_status mr_create(const mr_problem *prob, void *cuda_stream, mr_ctx **out);
+void mr_destroy(mr_ctx *ctx);
+
+/* Initial grid: u0 holds m x 2^(dJ) values at level J, lexicographic with x
+ * fastest; the full tree is projected (Sec. 2.2) and then adapted with
+ * threshold eta until no family can be deleted (Sec. 3.1.2). */
+mr_status mr_build(mr_ctx *ctx, const double *u0, int on_device, double eta);
+
+/* Replace the tree by the n given leaves (keys as above, values m x n).
+ * MR_EINVAL unless they tile the domain as a graded tree whose levels below
+ * jmin are all refined. */
+mr_status mr_set_leaves(mr_ctx *ctx, int64_t n, const uint64_t *keys, const double *values,
+                        int on_device);
+
+mr_status mr_num_leaves(const mr_ctx *ctx, int64_t *n);
+
+/* Copy the current leaves out (keys may be NULL).  cap is the capacity of
+ * `keys` (entries) and of each species row of `values`; MR_ENOMEM if short. */
+mr_status mr_get_leaves(mr_ctx *ctx, uint64_t *keys, double *values, int64_t cap, int64_t *n,
+                        int on_device);
+
+/* One grid adaptation (Sec. 3.1.2): projection, details d = u - P P u
+ * (Eq. detail) against eps_j = 2^((d/2)(j-J)) eta, refinement of tagged
+ * leaves, grading to the least graded tree, coarsening to a fixed point. */
+mr_status mr_adapt(mr_ctx *ctx, double eta);
+
+/* Reaction sub-step R_dt (Sec. 2.1): every leaf integrates u' = f(u) over dt
+ * with Radau5 (3-stage Radau IIA, simplified Newton, step-size control;
+ * rtol, atol > 0). */
+mr_status react_radau5(mr_ctx *ctx, double dt, double rtol, double atol);
+
+/* Diffusion sub-step D_dt (Sec. 2.1, Sec. 3.2.1): every species integrates
+ * u' = D_i L u with the ROCK4-type stabilized method (tol > 0). */
+mr_status diffuse_rock4(mr_ctx *ctx, double dt, double tol);
+
+/* One Strang step: mr_adapt(eta); R_{dt/2}; D_dt; R_{dt/2}. */
+mr_status strang_step(mr_ctx *ctx, double dt, double eta, double rtol, double atol,
+                      double rock_tol);
+
+mr_status mr_get_stats(const mr_ctx *ctx, mr_stats *out);
+
+/* Per-leaf complexity of the last react_radau5 call: f evaluations plus m
+ * per Jacobian (App. A counts the analytic BZ Jacobian as three). */
+mr_status mr_get_complexity(mr_ctx *ctx, int32_t *out, int64_t cap, int on_device);
+
+/* Integral of each species over the domain, sum over leaves h^d u_i (FP64). */
+mr_status mr_mass(mr_ctx *ctx, double *mass);
+
+/* Apply the species-free finite-volume leaf operator L (Eq. discretise,
+ * App. C; D_i L is the diffusion operator of species i) to one leaf vector
+ * u_in (length N) into out.  Also returns its Gershgorin bound in *rho
+ * (may be NULL).  For checking the operator the library builds. */
+mr_status mr_apply_operator(mr_ctx *ctx, const double *u_in, double *out, int on_device,
+                            double *rho);
+
+/* The library's ROCK4-type coefficients for s stages (5 <= s <= 152): the
+ * recurrence P_{j+1} = mu[j+1] P_j + nu[j+1] P_{j-1} + kap[j+1] z P_j
+ * (arrays of length s-3), the finishing quartic w[0..4] (w[0] = 1) and the
+ * embedded-estimate weights errc[0..3]; *ell = 0.336 s^2 - 2.7. */
+mr_status mr_rock4_coefficients(int s, double *mu, double *nu, double *kap, double *w,
+                                double *errc, double *ell);
+
+const char *mr_status_str(mr_status s);
+mr_status mr_last_error(const mr_ctx *ctx, char *buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

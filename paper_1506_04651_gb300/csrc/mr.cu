@@ -1,0 +1,918 @@
+// Multiresolution kernels: projection, details and thresholds, graded
+// refinement and coarsening, tree reconstruction, new-node prediction, leaf
+// lists, and the finite-volume leaf operator tables.
+//
+// Paper: Sec. 2.2 (dyadic tree, projection = exact average of the 2^d
+// children, prediction Eq. inter_1d by tensor product, details Eq. detail,
+// thresholds eps_j = 2^((d/2)(j-J)) eps, graded tree), Sec. 3.1.2 (refine
+// tagged leaves, tag extra nodes until graded, coarsen untagged families while
+// grading survives, repeat until no deletion), Eq. discretise and App. C
+// (finite-volume leaf operator with level-dependent coefficients).
+//
+// GPU formulation.  A tree is the set R of refined (internal) cells: the nodes
+// are the root and the children of R.  Grading holds iff every refined cell
+// (i, p), i >= 1, forces the cells (i-1, floor((p+o)/2)), o in {-1,0,1}^d, to
+// be refined.  One adaptation is then a single sweep from level J-1 down to
+// 0 over dense per-level byte flags:
+//   candidate(P) = refined before, or a tagged leaf, or forced from level i+1;
+//   keep(P)      = forced, or new, or tagged, or level < jmin;
+// kept cells force their level i-1 neighbours.  This reaches the same tree
+// as repeating "refine, grade, coarsen until no deletion": grading only adds
+// cells below a refined one, and a deletion only relaxes forcing one level
+// down.  Nodes are then renumbered without sorting: an exclusive scan over
+// the refined flags of all levels gives each refined cell its rank g, and its
+// children are nodes 1 + 2^d g ... 2^d (g + 1) (level-major Morton order).
+#include <math.h>
+#include <stdio.h>
+
+#include "mr_internal.cuh"
+
+namespace mrg {
+namespace {
+
+constexpr uint8_t F_OLD_INT = 1, F_TAG = 2, F_LEAF_TAG = 4;
+
+__device__ inline int mirror(int k, int j) {
+  if (k < 0) return -1 - k;
+  if (k >= (1 << j)) return (2 << j) - 1 - k;
+  return k;
+}
+
+// 1D prediction weight (Eq. inter_1d): child parity a, coarse offset o
+__device__ inline double wpred(int a, int o) {
+  if (o == 0) return 1.0;
+  return ((o == -1) == (a == 0)) ? 0.125 : -0.125;
+}
+
+struct Level {
+  int64_t doff[kMaxL + 2];
+  int64_t noff[kMaxL + 2];
+};
+
+// ------------------------------------------------------------ projection
+__global__ void k_scatter_leaves(const double* __restrict__ U, const int32_t* __restrict__ leaf_node,
+                                 double* __restrict__ V, int64_t N, int m, int64_t capL,
+                                 int64_t capN) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t n = leaf_node[r];
+    for (int i = 0; i < m; i++) V[i * capN + n] = U[i * capL + r];
+  }
+}
+
+template <int D>
+__global__ void k_project_level(double* __restrict__ V, const int32_t* __restrict__ first_child,
+                                int64_t lo, int64_t hi, int m, int64_t capN) {
+  for (int64_t n = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < hi;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int32_t fc = first_child[n];
+    if (fc < 0) continue;
+    for (int i = 0; i < m; i++) {
+      const double* v = V + i * capN + fc;
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < (1 << D); t++) s = __dadd_rn(s, v[t]);
+      V[i * capN + n] = s / (double)(1 << D);
+    }
+  }
+}
+
+// ------------------------------------------------------------ scales
+__global__ void k_scale(const double* __restrict__ U, int64_t N, int m, int64_t capL,
+                        unsigned long long* bits) {
+  for (int i = 0; i < m; i++) {
+    double mx = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+         r += (int64_t)gridDim.x * blockDim.x)
+      mx = fmax(mx, fabs(U[i * capL + r]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&bits[i], (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// prediction of node value from the 3^d stencil of its parent, literal tensor
+// sum in a fixed order with round-to-nearest products and sums (no fused
+// multiply-add), values looked up through the level-(j-1) map
+template <int D>
+__device__ inline double predict(const double* __restrict__ V, const int32_t* __restrict__ dmap_pl,
+                                 const int* k, int jm1, int64_t capN, int i) {
+  int par[3] = {k[0] >> 1, k[1] >> 1, D == 3 ? k[2] >> 1 : 0};
+  double s = 0.0;
+  constexpr int NST = D == 2 ? 9 : 27;
+#pragma unroll 1
+  for (int o = 0; o < NST; o++) {
+    int oo = o;
+    double w = 1.0;
+    int q[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+      int off = oo % 3 - 1;
+      oo /= 3;
+      q[a] = mirror(par[a] + off, jm1);
+      w = __dmul_rn(w, wpred(k[a] & 1, off));
+    }
+    int32_t idx = dmap_pl[morton<D>(q)];
+    if (idx < 0) return __longlong_as_double(0x7ff8000000000000ll);  // not graded: NaN
+    s = __dadd_rn(s, __dmul_rn(w, V[i * capN + idx]));
+  }
+  return s;
+}
+
+template <int D>
+__global__ void k_details(const double* __restrict__ V, const uint32_t* __restrict__ code,
+                          const uint8_t* __restrict__ lvl, const int32_t* __restrict__ dmap,
+                          Level L, int64_t nnodes, int m, int64_t capN, const double* __restrict__ scale,
+                          const double* __restrict__ eps_j, uint8_t* __restrict__ tag,
+                          double* __restrict__ delta_out, DevCounters* dc) {
+  for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nnodes;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int j = lvl[n];
+    int k[3];
+    unmorton<D>(code[n], k);
+    const int32_t* dm = dmap + L.doff[j - 1];
+    double dmax = 0.0;
+    for (int i = 0; i < m; i++) {
+      double p = predict<D>(V, dm, k, j - 1, capN, i);
+      double dd = fabs(__dadd_rn(V[i * capN + n], -p)) / scale[i];
+      dmax = fmax(dmax, dd);
+    }
+    if (isnan(dmax)) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
+    tag[n] = dmax >= eps_j[j];
+    if (delta_out) delta_out[n] = dmax;
+  }
+}
+
+// ------------------------------------------------------------ adaptation sweep
+__global__ void k_flags_init(const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
+                             const int32_t* __restrict__ first_child, const uint8_t* __restrict__ tag,
+                             Level L, int64_t nint, int J, uint8_t* __restrict__ state) {
+  // nodes of levels < J are the first nint nodes (level-major order)
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nint;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int j = lvl[n];
+    uint8_t f = 0;
+    if (first_child[n] >= 0) f |= F_OLD_INT;
+    if (n > 0 && tag[n]) {
+      f |= F_TAG;
+      if (first_child[n] < 0) f |= F_LEAF_TAG;
+    }
+    (void)J;
+    state[L.doff[j] + code[n]] = f;
+  }
+}
+
+template <int D>
+__global__ void k_sweep_level(const uint8_t* __restrict__ state, uint8_t* __restrict__ forced,
+                              uint8_t* __restrict__ final_, Level L, int i, int jmin) {
+  const int64_t n = (int64_t)1 << (D * i);
+  const int64_t base = L.doff[i];
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t st = state[base + p];
+    uint8_t fo = forced[base + p];
+    bool cand = (st & (F_OLD_INT | F_LEAF_TAG)) || fo;
+    bool keep = fo || !(st & F_OLD_INT) || (st & F_TAG) || i < jmin;
+    bool r = cand && keep;
+    final_[base + p] = r;
+    if (r && i >= 1) {
+      int k[3];
+      unmorton<D>((uint32_t)p, k);
+      const int64_t pb = L.doff[i - 1];
+      const int lim = 1 << i;
+      constexpr int NST = D == 2 ? 9 : 27;
+      for (int o = 0; o < NST; o++) {
+        int oo = o, q[3] = {0, 0, 0};
+        bool in = true;
+        for (int a = 0; a < D; a++) {
+          q[a] = k[a] + oo % 3 - 1;
+          oo /= 3;
+          in = in && q[a] >= 0 && q[a] < lim;
+          q[a] >>= 1;
+        }
+        if (in) forced[pb + morton<D>(q)] = 1;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ tree reconstruction
+__global__ void k_level_offsets(const int32_t* __restrict__ grank, const int32_t* total, Level L,
+                                int J, int D, DevCounters* dc) {
+  // level_internal[j] = refined cells in levels < j (exclusive scan at doff[j])
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    for (int j = 0; j < J; j++) dc->level_internal[j] = grank[L.doff[j]];
+    dc->level_internal[J] = *total;
+  }
+  (void)D;
+}
+
+__global__ void k_fill_int(int32_t* p, int64_t n, int32_t v) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x)
+    p[r] = v;
+}
+
+template <int D>
+__global__ void k_children(const uint8_t* __restrict__ final_, const int32_t* __restrict__ grank,
+                           Level L, int J, uint32_t* __restrict__ code, uint8_t* __restrict__ lvl,
+                           int32_t* __restrict__ first_child, int32_t* __restrict__ dmap) {
+  const int64_t nint = L.doff[J];
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nint;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (!final_[p]) continue;
+    int i = 0;
+    while (L.doff[i + 1] <= p) i++;
+    uint32_t c = (uint32_t)(p - L.doff[i]);
+    int64_t self;
+    if (i == 0) {
+      self = 0;
+    } else {
+      int64_t pp = L.doff[i - 1] + (c >> D);
+      self = 1 + ((int64_t)grank[pp] << D) + (c & ((1u << D) - 1));
+    }
+    int64_t fc = 1 + ((int64_t)grank[p] << D);
+    first_child[self] = (int32_t)fc;
+    for (int t = 0; t < (1 << D); t++) {
+      uint32_t cc = (c << D) | t;
+      code[fc + t] = cc;
+      lvl[fc + t] = (uint8_t)(i + 1);
+      dmap[L.doff[i + 1] + cc] = (int32_t)(fc + t);
+    }
+  }
+}
+
+__global__ void k_root(uint32_t* code, uint8_t* lvl, int32_t* dmap) {
+  code[0] = 0;
+  lvl[0] = 0;
+  dmap[0] = 0;
+}
+
+__global__ void k_leaf_flags(const int32_t* __restrict__ first_child, int64_t nn, int32_t* flag) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn;
+       n += (int64_t)gridDim.x * blockDim.x)
+    flag[n] = first_child[n] < 0;
+}
+
+__global__ void k_leaf_lists(const int32_t* __restrict__ first_child, const int32_t* __restrict__ lrank,
+                             int64_t nn, int32_t* __restrict__ leaf_node, int32_t* __restrict__ node_leaf) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    if (first_child[n] < 0) {
+      int32_t r = lrank[n];
+      leaf_node[r] = (int32_t)n;
+      node_leaf[n] = r;
+    } else {
+      node_leaf[n] = -1;
+    }
+  }
+}
+
+// values of the new tree, level j: old nodes keep their value, new nodes are
+// predicted from the new tree's level j-1 (whose stencils exist: graded)
+template <int D>
+__global__ void k_new_values(const uint32_t* __restrict__ code, int64_t lo, int64_t hi, int j,
+                             const int32_t* __restrict__ dmap_old, const int32_t* __restrict__ dmap_new,
+                             Level L, const double* __restrict__ Vold, double* __restrict__ Vnew,
+                             int m, int64_t capN, DevCounters* dc) {
+  for (int64_t n = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < hi;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c = code[n];
+    int32_t o = dmap_old[L.doff[j] + c];
+    if (o >= 0) {
+      for (int i = 0; i < m; i++) Vnew[i * capN + n] = Vold[i * capN + o];
+    } else {
+      int k[3];
+      unmorton<D>(c, k);
+      const int32_t* dm = dmap_new + L.doff[j - 1];
+      for (int i = 0; i < m; i++) {
+        double v = predict<D>(Vnew, dm, k, j - 1, capN, i);
+        if (isnan(v)) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
+        Vnew[i * capN + n] = v;
+      }
+    }
+  }
+}
+
+__global__ void k_gather_leaves(const double* __restrict__ V, const int32_t* __restrict__ leaf_node,
+                                double* __restrict__ U, int64_t N, int m, int64_t capL, int64_t capN) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t n = leaf_node[r];
+    for (int i = 0; i < m; i++) U[i * capL + r] = V[i * capN + n];
+  }
+}
+
+// ------------------------------------------------------------ full tree / explicit leaves
+template <int D>
+__global__ void k_full_values(const double* __restrict__ u0, const uint32_t* __restrict__ code,
+                              int64_t lo, int64_t N, int J, int m, int64_t capL,
+                              double* __restrict__ U) {
+  const int64_t nJ = (int64_t)1 << (D * J);
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int k[3];
+    unmorton<D>(code[lo + r], k);
+    int64_t lex = (int64_t)k[0] + ((int64_t)k[1] << J) + (D == 3 ? ((int64_t)k[2] << (2 * J)) : 0);
+    for (int i = 0; i < m; i++) U[i * capL + r] = u0[i * nJ + lex];
+  }
+}
+
+template <int D>
+__global__ void k_mark_ancestors(const uint64_t* __restrict__ keys, int64_t n, Level L, int J,
+                                 uint8_t* __restrict__ final_, DevCounters* dc) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t key = keys[r];
+    int j = (int)((key >> 48) & 15);
+    uint64_t s = key & ((1ull << 48) - 1);
+    if (j > J || (key >> 52) != 0 || (s >> (D * j)) != 0) {
+      atomicCAS(&dc->status, 0, (int)MR_EINVAL);
+      continue;
+    }
+    for (int i = j - 1; i >= 0; i--) final_[L.doff[i] + (uint32_t)(s >> (D * (j - i)))] = 1;
+  }
+}
+
+template <int D>
+__global__ void k_place_leaves(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
+                               int64_t n, Level L, const int32_t* __restrict__ dmap,
+                               const int32_t* __restrict__ node_leaf, int m, int64_t capL,
+                               double* __restrict__ U, int32_t* __restrict__ seen, DevCounters* dc) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t key = keys[r];
+    int j = (int)((key >> 48) & 15);
+    uint32_t c = (uint32_t)(key & ((1ull << 48) - 1));
+    int32_t idx = dmap[L.doff[j] + c];
+    int32_t li = idx >= 0 ? node_leaf[idx] : -1;
+    if (li < 0) {
+      atomicCAS(&dc->status, 0, (int)MR_EINVAL);
+      continue;
+    }
+    if (atomicAdd(&seen[li], 1) != 0) atomicCAS(&dc->status, 0, (int)MR_EINVAL);  // duplicate key
+    for (int i = 0; i < m; i++) U[i * capL + li] = vals[i * n + r];
+  }
+}
+
+template <int D>
+__global__ void k_check_graded(const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
+                               const int32_t* __restrict__ dmap, Level L, int64_t nn,
+                               DevCounters* dc) {
+  for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nn;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int j = lvl[n];
+    if (j < 2) continue;
+    int k[3];
+    unmorton<D>(code[n], k);
+    const int lim = 1 << (j - 1);
+    constexpr int NST = D == 2 ? 9 : 27;
+    for (int o = 0; o < NST; o++) {
+      int oo = o, q[3] = {0, 0, 0};
+      bool in = true;
+      for (int a = 0; a < D; a++) {
+        q[a] = (k[a] >> 1) + oo % 3 - 1;
+        oo /= 3;
+        in = in && q[a] >= 0 && q[a] < lim;
+      }
+      if (in && dmap[L.doff[j - 1] + morton<D>(q)] < 0) atomicCAS(&dc->status, 0, (int)MR_EINVAL);
+    }
+  }
+}
+
+// ------------------------------------------------------------ leaf operator tables
+template <int D>
+__global__ void k_classify(const int32_t* __restrict__ leaf_node, const uint32_t* __restrict__ code,
+                           const uint8_t* __restrict__ lvl, const int32_t* __restrict__ dmap,
+                           const int32_t* __restrict__ node_leaf, Level L, int64_t N, int64_t capL,
+                           int32_t* __restrict__ nbr, uint8_t* __restrict__ leaf_lvl,
+                           int32_t* __restrict__ irr_flag, unsigned long long* rho_bits) {
+  double rmax = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t n = leaf_node[r];
+    int j = lvl[n];
+    int k[3];
+    unmorton<D>(code[n], k);
+    leaf_lvl[r] = (uint8_t)j;
+    bool irr = false;
+    int inner = 0;
+    const int lim = 1 << j;
+    for (int f = 0; f < 2 * D; f++) {
+      int a = f >> 1, sg = (f & 1) ? 1 : -1;
+      int q[3] = {k[0], k[1], k[2]};
+      q[a] += sg;
+      int32_t nb = (int32_t)r;
+      if (q[a] >= 0 && q[a] < lim) {
+        int32_t idx = dmap[L.doff[j] + morton<D>(q)];
+        int32_t li = idx >= 0 ? node_leaf[idx] : -1;
+        if (li >= 0) {
+          nb = li;
+          inner++;
+        } else {
+          irr = true;
+        }
+      }
+      nbr[f * capL + r] = nb;
+    }
+    irr_flag[r] = irr;
+    if (!irr) rmax = fmax(rmax, 2.0 * inner * ldexp(1.0, 2 * j));
+  }
+  for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(rho_bits, (unsigned long long)__double_as_longlong(rmax));
+}
+
+__global__ void k_irr_index(const int32_t* __restrict__ irr_flag, const int32_t* __restrict__ irank,
+                            int64_t N, int64_t capL, int32_t* __restrict__ nbr,
+                            int32_t* __restrict__ irr_leaf) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if (!irr_flag[r]) continue;
+    int32_t row = irank[r];
+    irr_leaf[row] = (int32_t)r;
+    nbr[r] = -(row + 1);
+  }
+}
+
+template <int D>
+struct RowAcc {
+  static constexpr int kMax = D == 2 ? 96 : 384;
+  int n = 0;
+  bool overflow = false;
+  int32_t col[kMax];
+  double w[kMax];
+  __device__ void add(int32_t c, double v) {
+    for (int q = 0; q < n; q++)
+      if (col[q] == c) {
+        w[q] += v;
+        return;
+      }
+    if (n < kMax) {
+      col[n] = c;
+      w[n] = v;
+      n++;
+    } else {
+      overflow = true;
+    }
+  }
+};
+
+struct Item {
+  int j;
+  int k[3];
+  double w;
+};
+
+// value of cell (j, k) as a combination of leaf values: leaves directly,
+// internal cells as the mean of their children, absent cells by prediction
+template <int D>
+__device__ void vsym(const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf,
+                     const Level& L, int j0, const int* k0, double w0, RowAcc<D>& acc) {
+  constexpr int kStack = D == 2 ? 96 : 320;
+  Item st[kStack];
+  int sp = 0;
+  st[sp++] = Item{j0, {k0[0], k0[1], k0[2]}, w0};
+  while (sp > 0) {
+    Item it = st[--sp];
+    int k[3] = {0, 0, 0};
+    for (int a = 0; a < D; a++) k[a] = mirror(it.k[a], it.j);
+    int32_t idx = dmap[L.doff[it.j] + morton<D>(k)];
+    if (idx >= 0) {
+      int32_t li = node_leaf[idx];
+      if (li >= 0) {
+        acc.add(li, it.w);
+      } else {
+        for (int t = 0; t < (1 << D); t++) {
+          if (sp >= kStack) {
+            acc.overflow = true;
+            return;
+          }
+          Item c{it.j + 1, {0, 0, 0}, it.w / (double)(1 << D)};
+          for (int a = 0; a < D; a++) c.k[a] = 2 * k[a] + ((t >> a) & 1);
+          st[sp++] = c;
+        }
+      }
+    } else {
+      constexpr int NST = D == 2 ? 9 : 27;
+      for (int o = 0; o < NST; o++) {
+        if (sp >= kStack) {
+          acc.overflow = true;
+          return;
+        }
+        int oo = o;
+        Item c{it.j - 1, {0, 0, 0}, it.w};
+        for (int a = 0; a < D; a++) {
+          int off = oo % 3 - 1;
+          oo /= 3;
+          c.k[a] = (k[a] >> 1) + off;
+          c.w *= wpred(k[a] & 1, off);
+        }
+        st[sp++] = c;
+      }
+    }
+  }
+}
+
+template <int D>
+__device__ void irregular_row(int32_t r, const int32_t* __restrict__ leaf_node,
+                              const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
+                              const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf,
+                              const Level& L, RowAcc<D>& acc) {
+  int32_t n = leaf_node[r];
+  int j = lvl[n];
+  int k[3];
+  unmorton<D>(code[n], k);
+  const int lim = 1 << j;
+  const double ih2 = ldexp(1.0, 2 * j);
+  const double coef = ldexp(1.0, 2 * j + 1 - (D - 1));
+  for (int f = 0; f < 2 * D; f++) {
+    int a = f >> 1, sg = (f & 1) ? 1 : -1;
+    int q[3] = {k[0], k[1], k[2]};
+    q[a] += sg;
+    if (q[a] < 0 || q[a] >= lim) continue;  // homogeneous Neumann: zero flux
+    int32_t idx = dmap[L.doff[j] + morton<D>(q)];
+    if (idx < 0 || node_leaf[idx] >= 0) {
+      vsym<D>(dmap, node_leaf, L, j, q, ih2, acc);  // same-level leaf or predicted ghost
+      acc.add(r, -ih2);
+    } else {
+      // finer side: minus the mean of the fluxes into the 2^(d-1) touching children
+      for (int t = 0; t < (1 << D); t++) {
+        int c[3] = {0, 0, 0};
+        for (int b = 0; b < D; b++) c[b] = 2 * q[b] + ((t >> b) & 1);
+        if (c[a] != 2 * q[a] + (sg > 0 ? 0 : 1)) continue;
+        int g[3] = {c[0], c[1], c[2]};
+        g[a] -= sg;
+        vsym<D>(dmap, node_leaf, L, j + 1, g, -coef, acc);
+        vsym<D>(dmap, node_leaf, L, j + 1, c, coef, acc);
+      }
+    }
+  }
+}
+
+template <int D>
+__global__ void k_irr_rows(const int32_t* __restrict__ irr_leaf, int64_t nrows,
+                           const int32_t* __restrict__ leaf_node, const uint32_t* __restrict__ code,
+                           const uint8_t* __restrict__ lvl, const int32_t* __restrict__ dmap,
+                           const int32_t* __restrict__ node_leaf, Level L,
+                           int32_t* __restrict__ cnt, const int64_t* __restrict__ ptr,
+                           int32_t* __restrict__ col, double* __restrict__ wout,
+                           unsigned long long* rho_bits, DevCounters* dc) {
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < nrows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    RowAcc<D> acc;
+    irregular_row<D>(irr_leaf[row], leaf_node, code, lvl, dmap, node_leaf, L, acc);
+    if (acc.overflow) {
+      atomicExch(&dc->overflow, 1);
+      if (cnt) cnt[row] = 0;
+      continue;
+    }
+    // order by column (insertion sort), drop exact zeros
+    for (int a = 1; a < acc.n; a++) {
+      int32_t c = acc.col[a];
+      double w = acc.w[a];
+      int b = a - 1;
+      while (b >= 0 && acc.col[b] > c) {
+        acc.col[b + 1] = acc.col[b];
+        acc.w[b + 1] = acc.w[b];
+        b--;
+      }
+      acc.col[b + 1] = c;
+      acc.w[b + 1] = w;
+    }
+    int nz = 0;
+    double sa = 0.0;
+    for (int a = 0; a < acc.n; a++)
+      if (acc.w[a] != 0.0) {
+        if (!cnt) {
+          col[ptr[row] + nz] = acc.col[a];
+          wout[ptr[row] + nz] = acc.w[a];
+        }
+        nz++;
+        sa += fabs(acc.w[a]);
+      }
+    if (cnt) {
+      cnt[row] = nz;
+    } else {
+      atomicMax(rho_bits, (unsigned long long)__double_as_longlong(sa));
+    }
+  }
+}
+
+// ------------------------------------------------------------ mass
+__global__ void k_mass_partial(const double* __restrict__ U, const uint8_t* __restrict__ leaf_lvl,
+                               int64_t N, int m, int64_t capL, int D, double* __restrict__ part) {
+  __shared__ double sh[kBlock];
+  for (int i = 0; i < m; i++) {
+    double s = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+         r += (int64_t)gridDim.x * blockDim.x)
+      s += ldexp(1.0, -D * leaf_lvl[r]) * U[i * capL + r];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[i * gridDim.x + blockIdx.x] = sh[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_mass_final(const double* __restrict__ part, int nb, int m, double* __restrict__ out) {
+  int i = threadIdx.x;
+  if (i < m) {
+    double s = 0.0;
+    for (int b = 0; b < nb; b++) s += part[i * nb + b];
+    out[i] = s;
+  }
+}
+
+Level make_level(const mr_ctx* c, const TreeBuf& t) {
+  Level L;
+  for (int j = 0; j <= kMaxL + 1; j++) {
+    L.doff[j] = c->doff[j];
+    L.noff[j] = t.noff[j];
+  }
+  return L;
+}
+
+}  // namespace
+
+mr_status sync_counts(mr_ctx* c) {
+  MR_CUDA(c, cudaMemcpyAsync(&c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream));
+  MR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MR_OK;
+}
+
+// Build node arrays of buffer `dst` from c->fl_final (refined cells of levels < J).
+mr_status tree_from_final(mr_ctx* c, int dst, bool /*keep_values*/) {
+  TreeBuf& t = c->tb[dst];
+  const int D = c->d, J = c->J;
+  Level L = make_level(c, t);
+  int32_t* total = &c->dc->level_internal[kMaxL];
+  scan_u8(c, c->fl_final, c->grank, c->cap_dense_int, total);
+  k_level_offsets<<<1, 32, 0, c->stream>>>(c->grank, total, L, J, D, c->dc);
+  c->launches++;
+  MR_TRY(sync_counts(c));
+  // node offsets: level j+1 starts at 1 + 2^d (refined cells of levels < j)
+  t.noff[0] = 0;
+  t.noff[1] = 1;
+  for (int j = 1; j <= J; j++) t.noff[j + 1] = 1 + ((int64_t)c->hc.level_internal[j] << D);
+  for (int j = J + 2; j <= kMaxL + 1; j++) t.noff[j] = t.noff[J + 1];
+  t.nnodes = t.noff[J + 1];
+  if (t.nnodes > c->cap_nodes) return MR_ENOMEM;
+  L = make_level(c, t);
+  MR_CUDA(c, cudaMemsetAsync(t.dmap, 0xff, sizeof(int32_t) * c->cap_dense, c->stream));
+  k_fill_int<<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(t.first_child, t.nnodes, -1);
+  k_root<<<1, 1, 0, c->stream>>>(t.code, t.lvl, t.dmap);
+  if (D == 2)
+    k_children<2><<<grid_for(c->cap_dense_int), kBlock, 0, c->stream>>>(
+        c->fl_final, c->grank, L, J, t.code, t.lvl, t.first_child, t.dmap);
+  else
+    k_children<3><<<grid_for(c->cap_dense_int), kBlock, 0, c->stream>>>(
+        c->fl_final, c->grank, L, J, t.code, t.lvl, t.first_child, t.dmap);
+  k_leaf_flags<<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(t.first_child, t.nnodes, c->itmp);
+  scan_i32(c, c->itmp, t.node_leaf, t.nnodes, &c->dc->nleaves);
+  c->launches += 4;
+  MR_TRY(sync_counts(c));
+  t.nleaves = c->hc.nleaves;
+  if (t.nleaves > c->cap_leaves) return MR_ENOMEM;  // checked before any leaf is written
+  k_leaf_lists<<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(t.first_child, t.node_leaf, t.nnodes,
+                                                             t.leaf_node, t.node_leaf);
+  c->launches++;
+  // leaves per level: nodes of level j minus refined cells of level j
+  t.loff[0] = 0;
+  for (int j = 0; j <= J; j++) {
+    int64_t nodes_j = t.noff[j + 1] - t.noff[j];
+    int64_t ref_j = j < J ? (int64_t)c->hc.level_internal[j + 1] - c->hc.level_internal[j] : 0;
+    t.loff[j + 1] = t.loff[j] + nodes_j - ref_j;
+  }
+  for (int j = J + 2; j <= kMaxL + 1; j++) t.loff[j] = t.loff[J + 1];
+  c->tables_valid = false;
+  return MR_OK;
+}
+
+mr_status build_full(mr_ctx* c, const double* u0_dev) {
+  MR_CUDA(c, cudaMemsetAsync(c->fl_final, 1, c->cap_dense_int, c->stream));
+  mr_status s = tree_from_final(c, c->cur, false);
+  if (s) return s;
+  TreeBuf& t = c->tb[c->cur];
+  if (c->d == 2)
+    k_full_values<2><<<grid_for(t.nleaves), kBlock, 0, c->stream>>>(
+        u0_dev, t.code, t.noff[c->J], t.nleaves, c->J, c->m, c->cap_leaves, t.U);
+  else
+    k_full_values<3><<<grid_for(t.nleaves), kBlock, 0, c->stream>>>(
+        u0_dev, t.code, t.noff[c->J], t.nleaves, c->J, c->m, c->cap_leaves, t.U);
+  c->launches++;
+  MR_CUDA(c, cudaGetLastError());
+  return MR_OK;
+}
+
+mr_status set_leaves(mr_ctx* c, int64_t n, const uint64_t* keys_dev, const double* vals_dev) {
+  const int D = c->d;
+  MR_CUDA(c, cudaMemsetAsync(c->fl_final, 0, c->cap_dense_int, c->stream));
+  MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
+  TreeBuf& t = c->tb[c->cur];
+  Level L = make_level(c, t);
+  if (D == 2)
+    k_mark_ancestors<2><<<grid_for(n), kBlock, 0, c->stream>>>(keys_dev, n, L, c->J, c->fl_final, c->dc);
+  else
+    k_mark_ancestors<3><<<grid_for(n), kBlock, 0, c->stream>>>(keys_dev, n, L, c->J, c->fl_final, c->dc);
+  c->launches++;
+  MR_TRY(sync_counts(c));
+  if (c->hc.status) return MR_EINVAL;
+  mr_status s = tree_from_final(c, c->cur, false);
+  if (s) return s;
+  if (t.nleaves != n) return MR_EINVAL;
+  for (int j = 0; j < c->jmin; j++)
+    if (c->hc.level_internal[j + 1] - c->hc.level_internal[j] != c->n_level[j]) return MR_EINVAL;
+  L = make_level(c, t);
+  MR_CUDA(c, cudaMemsetAsync(c->itmp, 0, sizeof(int32_t) * n, c->stream));
+  if (D == 2) {
+    k_place_leaves<2><<<grid_for(n), kBlock, 0, c->stream>>>(keys_dev, vals_dev, n, L, t.dmap,
+                                                             t.node_leaf, c->m, c->cap_leaves, t.U, c->itmp, c->dc);
+    k_check_graded<2><<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(t.code, t.lvl, t.dmap, L, t.nnodes, c->dc);
+  } else {
+    k_place_leaves<3><<<grid_for(n), kBlock, 0, c->stream>>>(keys_dev, vals_dev, n, L, t.dmap,
+                                                             t.node_leaf, c->m, c->cap_leaves, t.U, c->itmp, c->dc);
+    k_check_graded<3><<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(t.code, t.lvl, t.dmap, L, t.nnodes, c->dc);
+  }
+  c->launches += 2;
+  MR_TRY(sync_counts(c));
+  return c->hc.status ? MR_EINVAL : MR_OK;
+}
+
+// project the current leaves to all nodes: V = leaf values, then bottom-up means
+static void project(mr_ctx* c, const TreeBuf& t) {
+  k_scatter_leaves<<<grid_for(t.nleaves), kBlock, 0, c->stream>>>(t.U, t.leaf_node, c->V, t.nleaves,
+                                                                  c->m, c->cap_leaves, c->cap_nodes);
+  c->launches++;
+  for (int j = c->J - 1; j >= 0; j--) {
+    int64_t lo = t.noff[j], hi = t.noff[j + 1];
+    if (c->d == 2)
+      k_project_level<2><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(c->V, t.first_child, lo, hi,
+                                                                       c->m, c->cap_nodes);
+    else
+      k_project_level<3><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(c->V, t.first_child, lo, hi,
+                                                                       c->m, c->cap_nodes);
+    c->launches++;
+  }
+}
+
+mr_status adapt(mr_ctx* c, double eta) {
+  const int D = c->d, J = c->J, m = c->m;
+  const int src = c->cur, dst = 1 - c->cur;
+  TreeBuf& t = c->tb[src];
+  Level L = make_level(c, t);
+  MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
+  project(c, t);
+  // scales s_i = max over leaves |u_i|
+  MR_CUDA(c, cudaMemsetAsync(c->dc->scale_bits, 0, sizeof(c->dc->scale_bits), c->stream));
+  k_scale<<<grid_for(t.nleaves), kBlock, 0, c->stream>>>(t.U, t.nleaves, m, c->cap_leaves,
+                                                          c->dc->scale_bits);
+  c->launches++;
+  MR_TRY(sync_counts(c));
+  double hs[kMaxM + kMaxL + 2];
+  for (int i = 0; i < m; i++) {
+    double s;
+    memcpy(&s, &c->hc.scale_bits[i], sizeof s);
+    hs[i] = fmax(s, 1e-30);
+  }
+  for (int j = 0; j <= J; j++) hs[kMaxM + j] = eta * pow(2.0, 0.5 * D * (j - J));
+  if (c->hc.status) return (mr_status)c->hc.status;
+  double* dpar = c->red_out;  // small device parameter block
+  MR_CUDA(c, cudaMemcpyAsync(dpar, hs, sizeof(double) * (kMaxM + J + 1), cudaMemcpyHostToDevice, c->stream));
+  if (D == 2)
+    k_details<2><<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(
+        c->V, t.code, t.lvl, t.dmap, L, t.nnodes, m, c->cap_nodes, dpar, dpar + kMaxM, c->tag, nullptr, c->dc);
+  else
+    k_details<3><<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(
+        c->V, t.code, t.lvl, t.dmap, L, t.nnodes, m, c->cap_nodes, dpar, dpar + kMaxM, c->tag, nullptr, c->dc);
+  c->launches++;
+  // flags and the level sweep
+  MR_CUDA(c, cudaMemsetAsync(c->fl_state, 0, c->cap_dense_int, c->stream));
+  MR_CUDA(c, cudaMemsetAsync(c->fl_forced, 0, c->cap_dense_int, c->stream));
+  k_flags_init<<<grid_for(t.noff[J]), kBlock, 0, c->stream>>>(t.code, t.lvl, t.first_child, c->tag, L,
+                                                             t.noff[J], J, c->fl_state);
+  c->launches++;
+  for (int i = J - 1; i >= 0; i--) {
+    if (D == 2)
+      k_sweep_level<2><<<grid_for(c->n_level[i]), kBlock, 0, c->stream>>>(c->fl_state, c->fl_forced,
+                                                                          c->fl_final, L, i, c->jmin);
+    else
+      k_sweep_level<3><<<grid_for(c->n_level[i]), kBlock, 0, c->stream>>>(c->fl_state, c->fl_forced,
+                                                                          c->fl_final, L, i, c->jmin);
+    c->launches++;
+  }
+  mr_status s = tree_from_final(c, dst, true);
+  if (s) return s;
+  TreeBuf& nt = c->tb[dst];
+  Level Ln = make_level(c, nt);
+  for (int j = 0; j <= J; j++) {
+    int64_t lo = nt.noff[j], hi = nt.noff[j + 1];
+    if (hi <= lo) continue;
+    if (D == 2)
+      k_new_values<2><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(nt.code, lo, hi, j, t.dmap, nt.dmap, Ln,
+                                                                   c->V, c->Vnew, m, c->cap_nodes, c->dc);
+    else
+      k_new_values<3><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(nt.code, lo, hi, j, t.dmap, nt.dmap, Ln,
+                                                                   c->V, c->Vnew, m, c->cap_nodes, c->dc);
+    c->launches++;
+  }
+  k_gather_leaves<<<grid_for(nt.nleaves), kBlock, 0, c->stream>>>(c->Vnew, nt.leaf_node, nt.U, nt.nleaves,
+                                                                 m, c->cap_leaves, c->cap_nodes);
+  c->launches++;
+  MR_CUDA(c, cudaGetLastError());
+  MR_TRY(sync_counts(c));
+  if (c->hc.status) {
+    c->last_error = "adaptation met a missing prediction stencil";
+    return (mr_status)c->hc.status;
+  }
+  c->cur = dst;
+  c->tables_valid = false;
+  return MR_OK;
+}
+
+mr_status build_tables(mr_ctx* c) {
+  if (c->tables_valid) return MR_OK;
+  TreeBuf& t = c->tb[c->cur];
+  const int D = c->d;
+  const int64_t N = t.nleaves;
+  Level L = make_level(c, t);
+  MR_CUDA(c, cudaMemsetAsync(c->rho_bits, 0, sizeof(unsigned long long), c->stream));
+  MR_CUDA(c, cudaMemsetAsync(&c->dc->overflow, 0, sizeof(int), c->stream));
+  int32_t* irr_flag = c->itmp;
+  if (D == 2)
+    k_classify<2><<<grid_for(N), kBlock, 0, c->stream>>>(t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, N,
+                                                         c->cap_leaves, c->nbr, c->leaf_lvl, irr_flag, c->rho_bits);
+  else
+    k_classify<3><<<grid_for(N), kBlock, 0, c->stream>>>(t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, N,
+                                                         c->cap_leaves, c->nbr, c->leaf_lvl, irr_flag, c->rho_bits);
+  int32_t* irank = c->itmp + c->cap_leaves;
+  scan_i32(c, irr_flag, irank, N, &c->dc->irr_rows);
+  k_irr_index<<<grid_for(N), kBlock, 0, c->stream>>>(irr_flag, irank, N, c->cap_leaves, c->nbr, c->irr_leaf);
+  c->launches += 2;
+  MR_TRY(sync_counts(c));
+  const int64_t nrows = c->hc.irr_rows;
+  if (nrows > 0) {
+    if (D == 2)
+      k_irr_rows<2><<<grid_for(nrows, 128), 128, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
+                                                                 t.dmap, t.node_leaf, L, c->irr_cnt, nullptr,
+                                                                 nullptr, nullptr, c->rho_bits, c->dc);
+    else
+      k_irr_rows<3><<<grid_for(nrows, 64), 64, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
+                                                               t.dmap, t.node_leaf, L, c->irr_cnt, nullptr,
+                                                               nullptr, nullptr, c->rho_bits, c->dc);
+    scan_i32_to_i64(c, c->irr_cnt, c->irr_ptr, nrows, &c->dc->irr_nnz);
+    c->launches++;
+    MR_TRY(sync_counts(c));
+    if (c->hc.overflow) {
+      c->last_error = "irregular operator row exceeds its local capacity";
+      return MR_ESTATE;
+    }
+    const int64_t nnz = c->hc.irr_nnz;
+    if (nnz > c->irr_cap) {
+      cudaFree(c->irr_col);
+      cudaFree(c->irr_w);
+      c->irr_cap = nnz + nnz / 2 + 1024;
+      MR_CUDA(c, cudaMalloc(&c->irr_col, sizeof(int32_t) * c->irr_cap));
+      MR_CUDA(c, cudaMalloc(&c->irr_w, sizeof(double) * c->irr_cap));
+    }
+    MR_CUDA(c, cudaMemcpyAsync(c->irr_ptr + nrows, &c->dc->irr_nnz, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                               c->stream));
+    if (D == 2)
+      k_irr_rows<2><<<grid_for(nrows, 128), 128, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
+                                                                 t.dmap, t.node_leaf, L, nullptr, c->irr_ptr,
+                                                                 c->irr_col, c->irr_w, c->rho_bits, c->dc);
+    else
+      k_irr_rows<3><<<grid_for(nrows, 64), 64, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
+                                                               t.dmap, t.node_leaf, L, nullptr, c->irr_ptr,
+                                                               c->irr_col, c->irr_w, c->rho_bits, c->dc);
+    c->launches++;
+  } else {
+    c->hc.irr_nnz = 0;
+  }
+  unsigned long long rb = 0;
+  MR_CUDA(c, cudaMemcpyAsync(&rb, c->rho_bits, sizeof rb, cudaMemcpyDeviceToHost, c->stream));
+  MR_CUDA(c, cudaStreamSynchronize(c->stream));
+  memcpy(&c->rho, &rb, sizeof rb);
+  c->stats.irregular_rows = nrows;
+  c->stats.irregular_nnz = c->hc.irr_nnz;
+  c->stats.rock_rho = c->rho;
+  c->tables_valid = true;
+  return MR_OK;
+}
+
+mr_status mass(mr_ctx* c, double* out_host) {
+  mr_status s = build_tables(c);  // leaf levels
+  if (s) return s;
+  TreeBuf& t = c->tb[c->cur];
+  const int nb = 152;
+  k_mass_partial<<<nb, kBlock, 0, c->stream>>>(t.U, c->leaf_lvl, t.nleaves, c->m, c->cap_leaves, c->d, c->red);
+  k_mass_final<<<1, 32, 0, c->stream>>>(c->red, nb, c->m, c->red_out);
+  c->launches += 2;
+  MR_CUDA(c, cudaMemcpyAsync(out_host, c->red_out, sizeof(double) * c->m, cudaMemcpyDeviceToHost, c->stream));
+  MR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MR_OK;
+}
+
+}  // namespace mrg

@@ -1,0 +1,230 @@
+"""Python binding of the C-ABI in include/mr.h (argument marshalling only).
+
+Every computation happens in the sm_103a kernels of libmrgb300.so; this module
+only converts NumPy arrays / torch tensors to pointers.  It raises if the
+native library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MR_OK = 0
+MR_MODEL_BZ, MR_MODEL_NAGUMO = 1, 2
+MR_FP64, MR_MIXED = 0, 1
+MAX_SPECIES, MAX_LEVEL = 16, 16
+
+STATUS = {0: "MR_OK", -1: "MR_EINVAL", -2: "MR_ENOMEM", -3: "MR_ECUDA", -4: "MR_ESTATE",
+          -10: "MR_ERADAU_HMIN", -11: "MR_ERADAU_MAXSTEPS", -12: "MR_ERADAU_SINGULAR",
+          -20: "MR_EROCK_STEP", -30: "MR_ENONFINITE", -40: "MR_ETIMEOUT"}
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("J", C.c_int), ("jmin", C.c_int), ("m", C.c_int),
+                ("model", C.c_int), ("nparams", C.c_int), ("precision", C.c_int),
+                ("reserved", C.c_int), ("params", C.c_double * 8),
+                ("D", C.c_double * MAX_SPECIES), ("max_leaves", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("leaves", C.c_int64), ("nodes", C.c_int64),
+                ("leaves_per_level", C.c_int64 * (MAX_LEVEL + 1)),
+                ("compression_ratio", C.c_double)] + \
+               [(n, C.c_int64) for n in ("radau_fev", "radau_jac", "radau_steps", "radau_accept",
+                                         "radau_reject", "radau_newton", "radau_dec",
+                                         "rock_steps", "rock_reject", "rock_stages", "rock_matvec")] + \
+               [("rock_smax", C.c_int32), ("reserved0", C.c_int32), ("rock_rho", C.c_double),
+                ("irregular_rows", C.c_int64), ("irregular_nnz", C.c_int64),
+                ("ms_adapt", C.c_double), ("ms_react", C.c_double), ("ms_diffuse", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if name == "leaves_per_level" else v
+        return out
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree libmrgb300.so (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"native library missing: {path}; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        vp, dp, i64, i64p = C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)
+        sig = {
+            "mr_create": [C.POINTER(Problem), vp, C.POINTER(C.c_void_p)],
+            "mr_build": [vp, dp, C.c_int, C.c_double],
+            "mr_set_leaves": [vp, i64, vp, dp, C.c_int],
+            "mr_num_leaves": [vp, i64p],
+            "mr_get_leaves": [vp, vp, dp, i64, i64p, C.c_int],
+            "mr_adapt": [vp, C.c_double],
+            "react_radau5": [vp, C.c_double, C.c_double, C.c_double],
+            "diffuse_rock4": [vp, C.c_double, C.c_double],
+            "strang_step": [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double],
+            "mr_get_stats": [vp, C.POINTER(Stats)],
+            "mr_get_complexity": [vp, vp, i64, C.c_int],
+            "mr_mass": [vp, dp],
+            "mr_apply_operator": [vp, dp, dp, C.c_int, C.POINTER(C.c_double)],
+            "mr_rock4_coefficients": [C.c_int, dp, dp, dp, dp, dp, C.POINTER(C.c_double)],
+            "mr_last_error": [vp, C.c_char_p, C.c_size_t],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.mr_destroy.argtypes = [vp]
+        L.mr_destroy.restype = None
+        L.mr_status_str.argtypes = [C.c_int]
+        L.mr_status_str.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class MRError(RuntimeError):
+    def __init__(self, code, where, msg=""):
+        super().__init__(f"{where}: {STATUS.get(code, code)} {msg}".strip())
+        self.code = code
+
+
+def _ptr(a):
+    """(pointer, on_device) of a NumPy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    return a.data_ptr(), int(a.is_cuda)
+
+
+def problem(dim, J, model="bz", params=None, D=None, jmin=2, precision=MR_FP64, max_leaves=0):
+    p = Problem()
+    p.dim, p.J, p.jmin, p.precision, p.max_leaves = dim, J, jmin, precision, max_leaves
+    if model == "bz":
+        p.model, p.m = MR_MODEL_BZ, 3
+        params = params if params is not None else (1e-2, 1e-5, 1.6, 2e-3)
+        D = D if D is not None else (2.5e-3, 2.5e-3, 1.5e-3)
+    elif model == "nagumo":
+        p.model, p.m = MR_MODEL_NAGUMO, 1
+        params = params if params is not None else (10.0,)
+        D = D if D is not None else (0.1,)
+    else:
+        raise ValueError(model)
+    p.nparams = len(params)
+    for i, v in enumerate(params):
+        p.params[i] = v
+    for i, v in enumerate(D):
+        p.D[i] = v
+    return p
+
+
+class Context:
+    """One problem on one GPU (owns the device memory of mr_create)."""
+
+    def __init__(self, prob: Problem, stream=None):
+        h = C.c_void_p()
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        rc = lib().mr_create(C.byref(prob), C.c_void_p(s), C.byref(h))
+        if rc:
+            raise MRError(rc, "mr_create")
+        self.h, self.prob, self.m = h, prob, prob.m
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mr_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _check(self, rc, where):
+        if rc:
+            buf = C.create_string_buffer(256)
+            lib().mr_last_error(self.h, buf, 256)
+            raise MRError(rc, where, buf.value.decode())
+        return rc
+
+    def build(self, u0, eta):
+        p, dev = _ptr(u0)
+        return self._check(lib().mr_build(self.h, C.c_void_p(p), dev, eta), "mr_build")
+
+    def set_leaves(self, keys, values):
+        kp, kd = _ptr(keys)
+        vp, vd = _ptr(values)
+        assert kd == vd
+        return self._check(lib().mr_set_leaves(self.h, len(keys), C.c_void_p(kp), C.c_void_p(vp), kd),
+                           "mr_set_leaves")
+
+    def num_leaves(self):
+        n = C.c_int64()
+        self._check(lib().mr_num_leaves(self.h, C.byref(n)), "mr_num_leaves")
+        return n.value
+
+    def leaves(self, keys_out=None, values_out=None):
+        n = self.num_leaves()
+        keys = keys_out if keys_out is not None else np.zeros(n, dtype=np.uint64)
+        vals = values_out if values_out is not None else np.zeros((self.m, n))
+        kp, kd = _ptr(keys)
+        vp, vd = _ptr(vals)
+        cnt = C.c_int64()
+        self._check(lib().mr_get_leaves(self.h, C.c_void_p(kp), C.c_void_p(vp), n, C.byref(cnt), vd),
+                    "mr_get_leaves")
+        return keys, vals
+
+    def adapt(self, eta):
+        return self._check(lib().mr_adapt(self.h, eta), "mr_adapt")
+
+    def react(self, dt, rtol=1e-6, atol=1e-6):
+        return self._check(lib().react_radau5(self.h, dt, rtol, atol), "react_radau5")
+
+    def diffuse(self, dt, tol=1e-6):
+        return self._check(lib().diffuse_rock4(self.h, dt, tol), "diffuse_rock4")
+
+    def strang(self, dt, eta, rtol=1e-6, atol=1e-6, rock_tol=1e-6):
+        return self._check(lib().strang_step(self.h, dt, eta, rtol, atol, rock_tol), "strang_step")
+
+    def stats(self):
+        s = Stats()
+        self._check(lib().mr_get_stats(self.h, C.byref(s)), "mr_get_stats")
+        return s.as_dict()
+
+    def complexity(self):
+        out = np.zeros(self.num_leaves(), dtype=np.int32)
+        self._check(lib().mr_get_complexity(self.h, C.c_void_p(out.ctypes.data), len(out), 0),
+                    "mr_get_complexity")
+        return out
+
+    def mass(self):
+        out = np.zeros(self.m)
+        self._check(lib().mr_mass(self.h, C.c_void_p(out.ctypes.data)), "mr_mass")
+        return out
+
+    def apply_operator(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros_like(u)
+        rho = C.c_double()
+        self._check(lib().mr_apply_operator(self.h, C.c_void_p(u.ctypes.data), C.c_void_p(out.ctypes.data),
+                                            0, C.byref(rho)), "mr_apply_operator")
+        return out, rho.value
+
+
+def rock4_coefficients(s):
+    n = s - 4
+    mu, nu, kap = np.zeros(n + 1), np.zeros(n + 1), np.zeros(n + 1)
+    w, errc = np.zeros(5), np.zeros(4)
+    ell = C.c_double()
+    rc = lib().mr_rock4_coefficients(s, *(C.c_void_p(a.ctypes.data) for a in (mu, nu, kap, w, errc)),
+                                     C.byref(ell))
+    if rc:
+        raise MRError(rc, "mr_rock4_coefficients")
+    return dict(mu=mu, nu=nu, kap=kap, w=w, errc=errc, ell=ell.value)
+
+
+def status_str(code):
+    return lib().mr_status_str(code).decode()

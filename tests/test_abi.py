@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/mr.h declares (no GPU needed).  The host-side ROCK4-type coefficient
+construction of the library is compared with the oracle's independent one."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_1506_04651_gb300 import build as B
+    B.build()
+    from paper_1506_04651_gb300 import mr
+    return mr
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "mr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for want in ("mr_create", "mr_destroy", "mr_build", "mr_adapt", "react_radau5", "diffuse_rock4",
+                 "strang_step", "mr_get_leaves", "mr_set_leaves", "mr_get_stats", "mr_status_str"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(native):
+    L = native.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_status_strings(native):
+    for code in native.STATUS:
+        assert native.status_str(code)
+
+
+def test_invalid_problem_rejected_before_gpu_work(native):
+    p = native.problem(2, 10)
+    p.dim = 4
+    h = C.c_void_p()
+    assert native.lib().mr_create(C.byref(p), None, C.byref(h)) == -1
+    p = native.problem(3, 11)  # d*J > 30
+    assert native.lib().mr_create(C.byref(p), None, C.byref(h)) == -1
+
+
+@pytest.mark.parametrize("s", [5, 6, 9, 17, 40, 100, 152])
+def test_rock4_coefficients_match_oracle(native, s):
+    g = native.rock4_coefficients(s)
+    o = O.rock4_coeffs(s)
+    assert g["ell"] == o["ell"]
+    for k in ("mu", "nu", "kap"):
+        np.testing.assert_allclose(g[k], o[k], rtol=2e-12, atol=1e-15)
+    np.testing.assert_allclose(g["w"], o["w"], rtol=2e-12)
+    np.testing.assert_allclose(g["errc"], o["errc"], rtol=1e-10)

@@ -1,0 +1,242 @@
+"""GPU parity: every step of the hot path, run through the C-ABI on the GPU,
+against the oracle on identical seeded inputs.
+
+Tolerances (the design doc derives them): adaptation decisions are taken on both
+sides with the same FP64 detail arithmetic (same sum order, no fused
+multiply-add), so leaf sets and values after an adaptation must be identical;
+operator rows use dyadic weights, so the Gershgorin bound is exact and L u
+agrees to 1e-12 relative; one Radau5 / ROCK4 / Strang step agrees to 1e-9
+relative L-infinity per species (the bound the benchmark spec fixes); ten steps agree
+to 1e-6 relative L1.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1506_04651_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1506_04651_gb300 import mr as M
+    return M
+
+
+def rel_linf(a, b):
+    a, b = np.atleast_2d(a), np.atleast_2d(b)
+    return max(np.max(np.abs(a[i] - b[i])) / max(np.max(np.abs(b[i])), 1e-300) for i in range(len(b)))
+
+
+def rel_l1(a, b):
+    a, b = np.atleast_2d(a), np.atleast_2d(b)
+    return max(np.sum(np.abs(a[i] - b[i])) / max(np.sum(np.abs(b[i])), 1e-300) for i in range(len(b)))
+
+
+def oracle_tree(d, J, u0, eta, m=3, jmin=2):
+    T = O.Tree(d, J, m, jmin=jmin)
+    T.set_full(u0)
+    assert T.adapt(eta) == 0
+    return T
+
+
+def gpu_ctx(mr, d, J, model="bz", jmin=2, **kw):
+    return mr.Context(mr.problem(d, J, model=model, jmin=jmin, **kw))
+
+
+def load(ctx, T):
+    keys, vals = T.leaves()
+    ctx.set_leaves(keys, np.ascontiguousarray(vals))
+    return keys, vals
+
+
+CASES_2D = [(7, lambda J: I.bz_front_2d(J, 1), 0.0), (8, lambda J: I.bz_cross_2d(J, 2), 1e-3),
+            (9, lambda J: I.bz_cross_2d(J, 4), 3e-3)]
+
+
+@pytest.mark.parametrize("J,gen,eta", CASES_2D)
+def test_build_matches_oracle_exactly(mr, J, gen, eta):
+    u0 = gen(J)
+    T = oracle_tree(2, J, u0, eta)
+    ctx = gpu_ctx(mr, 2, J)
+    ctx.build(u0, eta)
+    k_o, v_o = T.leaves()
+    k_g, v_g = ctx.leaves()
+    assert np.array_equal(k_o, k_g)
+    assert np.array_equal(v_o, v_g)
+
+
+@pytest.mark.parametrize("J,gen,eta", CASES_2D[1:])
+def test_adapt_after_reaction_matches_oracle_exactly(mr, J, gen, eta):
+    md = O.make_model("bz")
+    T = oracle_tree(2, J, gen(J), eta)
+    T.react(md, 5e-4)  # move the fronts so the next adaptation refines and coarsens
+    ctx = gpu_ctx(mr, 2, J)
+    k0, _ = load(ctx, T)
+    assert T.adapt(eta) == 0
+    ctx.adapt(eta)
+    k_o, v_o = T.leaves()
+    k_g, v_g = ctx.leaves()
+    assert not np.array_equal(k0, k_o)
+    assert np.array_equal(k_o, k_g)
+    assert np.array_equal(v_o, v_g)
+
+
+@pytest.mark.parametrize("d,J", [(2, 8), (2, 10), (3, 5)])
+def test_operator_matches_oracle(mr, d, J):
+    u0 = I.bz_cross_2d(J, 2) if d == 2 else I.bz_sphere_3d(J, 3)
+    T = oracle_tree(d, J, u0, 1e-3)
+    ctx = gpu_ctx(mr, d, J)
+    load(ctx, T)
+    rp, col, val, rho = T.operator()
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal(len(rp) - 1)
+    want = np.add.reduceat(val * u[col], rp[:-1])
+    got, rho_g = ctx.apply_operator(u)
+    assert rho_g == rho
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    st = ctx.stats()
+    assert st["irregular_rows"] > 0
+
+
+@pytest.mark.parametrize("d,J,gen", [(2, 7, lambda J: I.bz_front_2d(J, 1)),
+                                     (2, 9, lambda J: I.bz_cross_2d(J, 2)),
+                                     (3, 5, lambda J: I.bz_sphere_3d(J, 3))])
+def test_react_matches_oracle(mr, d, J, gen):
+    md = O.make_model("bz")
+    T = oracle_tree(d, J, gen(J), 1e-3 if J > 7 else 0.0)
+    ctx = gpu_ctx(mr, d, J)
+    load(ctx, T)
+    rc, st_o, cx_o = T.react(md, 5e-4, want_complexity=True)
+    assert rc == 0
+    ctx.react(5e-4)
+    _, v_o = T.leaves()
+    _, v_g = ctx.leaves()
+    assert rel_linf(v_g, v_o) <= 1e-9
+    cx_g = ctx.complexity()
+    st_g = ctx.stats()
+    # same step/iteration structure on (almost) every cell
+    assert np.mean(cx_g == cx_o) > 0.999
+    assert cx_g.min() == cx_o.min() and cx_g.max() == cx_o.max()
+
+
+@pytest.mark.parametrize("d,J,gen", [(2, 7, lambda J: I.bz_front_2d(J, 1)),
+                                     (2, 9, lambda J: I.bz_cross_2d(J, 2)),
+                                     (3, 5, lambda J: I.bz_sphere_3d(J, 3))])
+def test_diffuse_matches_oracle_and_conserves_mass(mr, d, J, gen):
+    T = oracle_tree(d, J, gen(J), 1e-3 if J > 7 else 0.0)
+    ctx = gpu_ctx(mr, d, J)
+    load(ctx, T)
+    m0 = ctx.mass()
+    np.testing.assert_allclose(m0, T.mass(), rtol=1e-11)  # two summation orders
+    rc, st_o = T.diffuse(I.BZ_D, 1e-3, 1e-6)
+    assert rc == 0
+    ctx.diffuse(1e-3, 1e-6)
+    _, v_o = T.leaves()
+    _, v_g = ctx.leaves()
+    assert rel_linf(v_g, v_o) <= 1e-9
+    st_g = ctx.stats()
+    assert st_g["rock_steps"] == st_o["nsteps"] and st_g["rock_reject"] == st_o["nreject"]
+    np.testing.assert_allclose(ctx.mass(), m0, rtol=1e-12)  # the operator conserves mass
+
+
+def test_one_strang_step_uniform_128(mr):
+    """BZ, uniform 128 x 128 (J = 7, eta = 0), 1% seeded noise."""
+    md = O.make_model("bz")
+    u0 = I.bz_front_2d(7, 1)
+    T = oracle_tree(2, 7, u0, 0.0)
+    ctx = gpu_ctx(mr, 2, 7)
+    ctx.build(u0, 0.0)
+    assert T.strang(md, I.BZ_D, 1e-3, 0.0) == 0
+    ctx.strang(1e-3, 0.0)
+    k_o, v_o = T.leaves()
+    k_g, v_g = ctx.leaves()
+    assert np.array_equal(k_o, k_g) and len(k_g) == 128 * 128
+    assert rel_linf(v_g, v_o) <= 1e-9
+
+
+def test_ten_strang_steps_uniform_128(mr):
+    md = O.make_model("bz")
+    u0 = I.bz_front_2d(7, 1)
+    T = oracle_tree(2, 7, u0, 0.0)
+    ctx = gpu_ctx(mr, 2, 7)
+    ctx.build(u0, 0.0)
+    for _ in range(10):
+        assert T.strang(md, I.BZ_D, 1e-3, 0.0) == 0
+        ctx.strang(1e-3, 0.0)
+    _, v_o = T.leaves()
+    _, v_g = ctx.leaves()
+    assert rel_l1(v_g, v_o) <= 1e-6
+
+
+def test_adaptive_strang_steps(mr):
+    """Adaptive 2D case (J = 8, eta = 1e-3): identical grids step by step, values to
+    1e-9 after one step and 1e-6 (relative L1) after five."""
+    md = O.make_model("bz")
+    J, eta = 8, 1e-3
+    u0 = I.bz_cross_2d(J, 2)
+    T = oracle_tree(2, J, u0, eta)
+    ctx = gpu_ctx(mr, 2, J)
+    ctx.build(u0, eta)
+    for step in range(5):
+        assert T.strang(md, I.BZ_D, 1e-3, eta) == 0
+        ctx.strang(1e-3, eta)
+        k_o, v_o = T.leaves()
+        k_g, v_g = ctx.leaves()
+        assert np.array_equal(k_o, k_g)
+        if step == 0:
+            assert rel_linf(v_g, v_o) <= 1e-9
+    assert rel_l1(v_g, v_o) <= 1e-6
+
+
+def test_invalid_leaf_sets_are_rejected(mr):
+    ctx = gpu_ctx(mr, 2, 5)
+    T = oracle_tree(2, 5, I.bz_cross_2d(5, 2), 3e-3)
+    keys, vals = T.leaves()
+    with pytest.raises(mr.MRError) as e:
+        ctx.set_leaves(keys[1:], np.ascontiguousarray(vals[:, 1:]))  # hole in the tiling
+    assert e.value.code == -1
+    dup = keys.copy()
+    dup[1] = dup[0]
+    with pytest.raises(mr.MRError):
+        ctx.set_leaves(dup, vals)
+    # a level-jump of two (not graded)
+    T2 = O.Tree(2, 5, 3, jmin=2)
+    T2.set_full(np.ones((3, 1 << 10)))
+    T2.adapt(1.0)  # all leaves at level 2
+    k2, v2 = T2.leaves()
+    sel = k2 != k2[0]
+    first = int(k2[0])
+    j, k = O.key_decode(2, first)
+    fine = []
+    for a in range(4):
+        for b in range(4):
+            fine.append(O.key(2, 4, [4 * k[0] + a, 4 * k[1] + b]))
+    bad_keys = np.concatenate([k2[sel], np.array(fine, dtype=np.uint64)])
+    bad_vals = np.ones((3, len(bad_keys)))
+    with pytest.raises(mr.MRError):
+        ctx.set_leaves(bad_keys, bad_vals)
+    ctx.set_leaves(keys, vals)  # a valid tree is still accepted afterwards
+    assert ctx.num_leaves() == len(keys)
+
+
+def test_nagumo_model_parity(mr):
+    md = O.make_model("nagumo")
+    J = 7
+    x = (np.arange(1 << J) + 0.5) / (1 << J)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    u0 = (0.5 * (1 - np.tanh((np.hypot(X - 0.3, Y - 0.4) - 0.2) / 0.02))).ravel()[None, :]
+    T = O.Tree(2, J, 1, jmin=2)
+    T.set_full(u0)
+    T.adapt(1e-3)
+    ctx = gpu_ctx(mr, 2, J, model="nagumo")
+    ctx.build(u0, 1e-3)
+    assert T.strang(md, [0.1], 1e-2, 1e-3) == 0
+    ctx.strang(1e-2, 1e-3)
+    k_o, v_o = T.leaves()
+    k_g, v_g = ctx.leaves()
+    assert np.array_equal(k_o, k_g)
+    assert rel_linf(v_g, v_o) <= 1e-9
