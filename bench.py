@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: leaf-cell Strang updates per second on one GB300.
+
+One "step" is one Strang step of the BZ reaction-diffusion system on the
+adaptive multiresolution grid: grid adaptation, R_{dt/2} (Radau5 per leaf),
+D_dt (ROCK4-type per species), R_{dt/2}.  One update is one leaf advanced
+through a whole step; value = sum over steps of the leaves / device time.
+
+Default workload (the one the metric is quoted on): 2D BZ, finest level
+J = 10 (1024^2), eta = 1e-3, two crossing tanh fronts (w = 0.02) with smooth
+seeded position noise, dt = 1e-3, rtol = atol = tol = 1e-6, FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...    (the CPU oracle on the host cores)
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the step does not shard); value = leaves of all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "leaf-cell Strang updates/s on 1 GB300, mixed vs FP64 at rel-L1 ≤1e-5; % roofline"
+UNIT = "leaf-updates/s"
+
+WORKLOADS = {
+    "bz2d_J10_eta1e-3": dict(d=2, J=10, eta=1e-3, dt=1e-3, gen="cross", seed=2,
+                             desc="2D BZ, J=10 (1024^2 finest), eta=1e-3, graded, two crossing "
+                                  "tanh fronts (w=0.02) + smooth seeded noise, dt=1e-3, FP64"),
+    "bz2d_J7_uniform": dict(d=2, J=7, eta=0.0, dt=1e-3, gen="front", seed=1,
+                            desc="2D BZ, uniform 128^2 (J=7, eta=0), tanh front + 1% seeded noise, "
+                                 "dt=1e-3, FP64"),
+    "bz3d_J7_eta1e-2": dict(d=3, J=7, eta=1e-2, dt=1e-3, gen="sphere", seed=3,
+                            desc="3D BZ, J=7 (128^3 finest), eta=1e-2, spherical front r=0.3, "
+                                 "w=0.02 + smooth seeded noise, dt=1e-3, FP64"),
+}
+DEFAULT = "bz2d_J10_eta1e-3"
+TOL = 1e-6
+
+
+def initial_state(w):
+    from paper_1506_04651_gb300 import inputs as I
+    if w["gen"] == "cross":
+        return I.bz_cross_2d(w["J"], w["seed"])
+    if w["gen"] == "front":
+        return I.bz_front_2d(w["J"], w["seed"])
+    return I.bz_sphere_3d(w["J"], w["seed"])
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in self.rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(w, u0, budget_s=20.0, max_steps=100):
+    """The oracle as it stands (single-threaded C), Strang steps on the same
+    workload until the time budget is spent; returns (rate, steps, cores)."""
+    from oracle import oracle as O
+    from paper_1506_04651_gb300 import inputs as I
+    T = O.Tree(w["d"], w["J"], 3, jmin=2)
+    T.set_full(u0)
+    assert T.adapt(w["eta"]) == 0
+    md = O.make_model("bz")
+    leaves, t_tot, steps = 0, 0.0, 0
+    while steps < max_steps and t_tot < budget_s:
+        t0 = time.perf_counter()
+        rc = T.strang(md, I.BZ_D, w["dt"], w["eta"], TOL, TOL, TOL)
+        t_tot += time.perf_counter() - t0
+        assert rc == 0, rc
+        leaves += T.num_leaves()
+        steps += 1
+    return leaves / t_tot, steps, 1
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    u0 = initial_state(w)
+    budget = min(240.0, 20.0 + 2.0 * args.steps)
+    rate, steps, cores = cpu_oracle_rate(w, u0, budget_s=budget, max_steps=args.steps)
+    sample = f"first {steps} Strang steps of the workload from its initial grid (single-threaded C oracle)"
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+            "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, w):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1506_04651_gb300 import mr
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    stream = torch.cuda.current_stream()
+    u0 = initial_state(w)
+    ctx = mr.Context(mr.problem(w["d"], w["J"]), stream=stream)
+    ctx.build(torch.from_numpy(u0).to(dev), w["eta"])
+
+    def step():
+        ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+
+    for _ in range(args.warmup):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    st0 = ctx.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    leaves = 0
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+        leaves += ctx.stats()["leaves"]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    st1 = ctx.stats()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        n = torch.tensor([float(leaves)], device=dev)
+        pg.all_reduce(n, op=pg.ReduceOp.SUM)
+        total_leaves = n.item()
+    else:
+        total_leaves = leaves
+    value = total_leaves / (ms * 1e-3)
+
+    # kernel-level roofline figures over the timed region
+    rad_ms = st1["radau_kernel_ms"] - st0["radau_kernel_ms"]
+    rad_n = st1["radau_kernel_launches"] - st0["radau_kernel_launches"]
+    rad_fl = st1["radau_alg_flops"] - st0["radau_alg_flops"]
+    rock_ms = st1["rock_kernel_ms"] - st0["rock_kernel_ms"]
+    rock_n = st1["rock_kernel_launches"] - st0["rock_kernel_launches"]
+    rock_b = st1["rock_alg_bytes"] - st0["rock_alg_bytes"]
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    peaks = measured_peaks()
+    fp64_tf, fp64_mhz = mr.fp64_fma_rate()
+    hbm = peaks.get("hbm_gbs")
+    if rad_ms >= rock_ms:
+        ach = rad_fl / (rad_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_radau (Radau5, FP64)", "achieved": ach, "peak": fp64_tf,
+                "unit": "TFLOP/s", "frac": ach / fp64_tf, "traffic": None,
+                "peak_source": "measured FP64 FMA rate of this GPU (library probe, 2 flop/FMA)",
+                "launches": rad_n, "ms_per_launch": rad_ms / max(rad_n, 1)}
+    else:
+        ach = rock_b / (rock_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_rock (ROCK4 sweep, FP64)", "achieved": ach,
+                "peak": hbm or 6800.0, "unit": "GB/s", "frac": ach / (hbm or 6800.0), "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s",
+                "launches": rock_n, "ms_per_launch": rock_ms / max(rock_n, 1)}
+    kernels = {"radau": {"ms": rad_ms, "launches": rad_n, "tflops": rad_fl / max(rad_ms, 1e-9) / 1e9},
+               "rock": {"ms": rock_ms, "launches": rock_n,
+                        "gbs": rock_b / max(rock_ms, 1e-9) / 1e6},
+               "step_ms": ms / args.steps}
+
+    # end to end through the C-ABI with host buffers: state in from pinned host
+    # memory, one step, state out, every step
+    n0 = ctx.num_leaves()
+    cap = 1 << (w["d"] * w["J"])
+    hk = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    hv = torch.empty(3 * cap, dtype=torch.float64, pin_memory=True).numpy()
+    hk2 = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    hv2 = torch.empty(3 * cap, dtype=torch.float64, pin_memory=True).numpy()
+    keys, vals = ctx.leaves(hk[:n0], hv[:3 * n0].reshape(3, n0))
+    n_e2e = min(args.steps, 20)
+    h2d = d2h = 0
+    e2e_leaves = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        n = len(keys)
+        ctx.set_leaves(keys, vals)
+        h2d += keys.nbytes + vals.nbytes
+        step()
+        n = ctx.num_leaves()
+        e2e_leaves += n
+        keys, vals = ctx.leaves(hk2[:n], hv2[:3 * n].reshape(3, n))
+        d2h += keys.nbytes + vals.nbytes
+        hk, hk2, hv, hv2 = hk2, hk, hv2, hv
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": e2e_leaves / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
+           "d2h_bytes_per_step": d2h // n_e2e, "steps": n_e2e,
+           "note": "mr_set_leaves(host) + strang_step + mr_get_leaves(host) per step, wall clock"}
+
+    if pg:
+        pg.barrier()
+    if rank != 0:
+        ctx.close()
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, steps, cores = cpu_oracle_rate(w, initial_state(w), budget_s=20.0, max_steps=50)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {steps} Strang steps of the same workload from its initial grid "
+                         f"(single-threaded C oracle, ~20 s budget)"}
+    st = ctx.stats()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"],
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "leaves_last_step": st["leaves"], "compression_ratio": st["compression_ratio"],
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -95,6 +95,14 @@ typedef struct {
   int64_t irregular_rows, irregular_nnz;
   double ms_adapt, ms_react, ms_diffuse; /* device time of the last strang_step phases */
   int64_t kernel_launches;        /* cumulative kernels launched by this context */
+  /* cumulative since mr_create, from CUDA events around each launch on the
+   * context stream: the Radau5 kernel and the ROCK4 sweep kernel, with their
+   * algorithmic work (Radau5: FP64 operations of the source per counted
+   * event; ROCK4: bytes each sweep must move at least) */
+  double radau_kernel_ms, radau_alg_flops;
+  int64_t radau_kernel_launches;
+  double rock_kernel_ms, rock_alg_bytes;
+  int64_t rock_kernel_launches;
 } mr_stats;
 
 /* Create a context for `prob` on `cuda_stream` (a cudaStream_t or NULL).
@@ -161,6 +169,13 @@ mr_status mr_apply_operator(mr_ctx *ctx, const double *u_in, double *out, int on
  * embedded-estimate weights errc[0..3]; *ell = 0.336 s^2 - 2.7. */
 mr_status mr_rock4_coefficients(int s, double *mu, double *nu, double *kap, double *w,
                                 double *errc, double *ell);
+
+/* Measurement aid (no counterpart in the paper): FP64 fused multiply-add
+ * throughput of the current device in TFLOP/s (2 flops per FMA), from a
+ * kernel of independent FMA chains on every SM timed with CUDA events; used
+ * as the denominator of the Radau5 arithmetic roofline.  *mhz gets the SM
+ * clock the driver reports during the run (may be NULL). */
+mr_status mr_fp64_fma_rate(double *tflops, double *mhz);
 
 const char *mr_status_str(mr_status s);
 mr_status mr_last_error(const mr_ctx *ctx, char *buf, size_t n);

@@ -24,6 +24,18 @@ mr_status cuda_fail(mr_ctx* c, cudaError_t e, const char* where) {
 
 namespace {
 
+// independent FMA chains: 8 per thread, all SMs busy
+__global__ void k_fma_probe(double* out, int iters, double a, double b) {
+  double x[8];
+  for (int q = 0; q < 8; q++) x[q] = threadIdx.x * 1e-9 + q;
+  for (int it = 0; it < iters; it++)
+#pragma unroll
+    for (int q = 0; q < 8; q++) x[q] = fma(x[q], a, b);
+  double s = 0.0;
+  for (int q = 0; q < 8; q++) s += x[q];
+  if (s == 1.2345) out[0] = s;  // keeps the chains live
+}
+
 __global__ void k_export_keys(const int32_t* __restrict__ leaf_node, const uint32_t* __restrict__ code,
                               const uint8_t* __restrict__ lvl, int64_t N, uint64_t* __restrict__ keys) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
@@ -140,6 +152,41 @@ mr_status to_device(mr_ctx* c, const T* src, int64_t count, int on_device, T** d
 }
 
 }  // namespace
+
+mr_status fp64_probe(double* tflops, double* mhz) {
+  int dev = 0, nsm = 0, clk = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double)) != cudaSuccess) return MR_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = nsm * 8, threads = 256, iters = 4096;
+  k_fma_probe<<<blocks, threads>>>(out, 64, 0.999999, 1e-7);  // warm-up
+  float best = 1e30f;
+  for (int rep = 0; rep < 5; rep++) {
+    cudaEventRecord(e0);
+    k_fma_probe<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess) return MR_ECUDA;
+  *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  if (mhz) {
+    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
+    *mhz = clk / 1000.0;
+  }
+  return MR_OK;
+}
+
 }  // namespace mrg
 
 using namespace mrg;
@@ -212,6 +259,8 @@ mr_status mr_create(const mr_problem* p, void* stream, mr_ctx** out) {
   if (s == MR_OK) {
     for (int q = 0; q < 8; q++)
       if (cudaEventCreate(&c->ev[q]) != cudaSuccess) s = MR_ECUDA;
+    for (int q = 0; q < 2 * 256; q++)
+      if (cudaEventCreate(&c->tev[q]) != cudaSuccess) s = MR_ECUDA;
   }
   if (s) {
     free_all(c);
@@ -226,6 +275,7 @@ void mr_destroy(mr_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   for (int q = 0; q < 8; q++) cudaEventDestroy(c->ev[q]);
+  for (int q = 0; q < 2 * 256; q++) cudaEventDestroy(c->tev[q]);
   free_all(c);
   delete c;
 }
@@ -384,6 +434,11 @@ mr_status mr_apply_operator(mr_ctx* c, const double* u_in, double* out, int on_d
   if (o2) cudaFree(dout);
   if (!s && rho) *rho = c->rho;
   return s;
+}
+
+mr_status mr_fp64_fma_rate(double* tflops, double* mhz) {
+  if (!tflops) return MR_EINVAL;
+  return fp64_probe(tflops, mhz);
 }
 
 mr_status mr_rock4_coefficients(int s, double* mu, double* nu, double* kap, double* w, double* errc, double* ell) {

@@ -149,6 +149,7 @@ struct mr_ctx {
   mrg::DevCounters* dc = nullptr;
   mrg::DevCounters hc;               // host copy
   cudaEvent_t ev[8];
+  cudaEvent_t tev[2 * 256];           // per-launch timing pairs of the ROCK4 sweeps
   mr_stats stats;
   int64_t launches = 0;
   std::string last_error;
@@ -170,6 +171,7 @@ inline int grid_for(int64_t n, int block = kBlock) {
 }
 
 mr_status cuda_fail(mr_ctx* c, cudaError_t e, const char* where);
+mr_status fp64_probe(double* tflops, double* mhz);
 #define MR_CUDA(ctx, call)                                       \
   do {                                                           \
     cudaError_t _e = (call);                                     \

@@ -295,7 +295,27 @@ int rock4_coeffs(int s, double* mu, double* nu, double* kap, double* w, double* 
   return 0;
 }
 
-static void launch_rock(mr_ctx* c, const StageArgs& A, int64_t N, int nb) {
+// minimum bytes one sweep moves: per leaf the 2d neighbour indices and the
+// level, per species the vectors the mode reads once and writes once, plus
+// the merged rows of the leaves at level jumps
+static double sweep_bytes(const mr_ctx* c, const StageArgs& A, int64_t N) {
+  double per_leaf = 0.0;
+  for (int i = 0; i < A.nspec; i++) {
+    const SpecOp& o = A.op[i];
+    switch (A.mode) {
+      case M_STAGE: per_leaf += o.b ? 24 : 16; break;
+      case M_H3: per_leaf += 16; break;
+      case M_H2: per_leaf += 24; break;
+      case M_H1: per_leaf += 32; break;
+      case M_H0: per_leaf += 40; break;
+      default: per_leaf += 24;
+    }
+  }
+  return N * (per_leaf + 8.0 * c->d + 1.0) + 12.0 * c->stats.irregular_nnz + 8.0 * c->stats.irregular_rows;
+}
+
+static void launch_rock(mr_ctx* c, const StageArgs& A, int64_t N, int nb, int* nev = nullptr) {
+  if (nev && *nev < 256) cudaEventRecord(c->tev[2 * *nev], c->stream);
   if (c->d == 2)
     k_rock<2><<<nb, kBlock, 0, c->stream>>>(A, N, c->cap_leaves, c->nbr, c->leaf_lvl, c->irr_ptr, c->irr_col,
                                             c->irr_w, c->red);
@@ -303,6 +323,12 @@ static void launch_rock(mr_ctx* c, const StageArgs& A, int64_t N, int nb) {
     k_rock<3><<<nb, kBlock, 0, c->stream>>>(A, N, c->cap_leaves, c->nbr, c->leaf_lvl, c->irr_ptr, c->irr_col,
                                             c->irr_w, c->red);
   c->launches++;
+  if (nev && *nev < 256) {
+    cudaEventRecord(c->tev[2 * *nev + 1], c->stream);
+    c->stats.rock_alg_bytes += sweep_bytes(c, A, N);
+    c->stats.rock_kernel_launches++;
+    (*nev)++;
+  }
 }
 
 mr_status apply_operator(mr_ctx* c, const double* in, double* out) {
@@ -354,7 +380,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   S.rock_smax = 0;
   auto W = [&](int q, int i) { return c->work[q] + (int64_t)i * cap; };
   for (int round = 0;; round++) {
-    int act[kMaxM], na = 0, nmax = 0;
+    int act[kMaxM], na = 0, nmax = 0, nev = 0;
     for (int i = 0; i < m; i++) {
       if (sp[i].done) continue;
       Sp& p = sp[i];
@@ -410,7 +436,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
         o.cl = p.C->kap[j] * hd;
         S.rock_matvec++;
       }
-      launch_rock(c, A, N, nb);
+      launch_rock(c, A, N, nb, &nev);
     }
     // Horner steps and the error estimate
     for (int mode = M_H3; mode <= M_FSAL; mode++) {
@@ -445,13 +471,18 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
         }
         S.rock_matvec++;
       }
-      launch_rock(c, A, N, nb);
+      launch_rock(c, A, N, nb, &nev);
     }
     k_reduce_rows<<<1, kBlock, 0, c->stream>>>(c->red, nb, na, c->red_out);
     c->launches++;
     double err2[kMaxM];
     MR_CUDA(c, cudaMemcpyAsync(err2, c->red_out, sizeof(double) * na, cudaMemcpyDeviceToHost, c->stream));
     MR_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < nev; q++) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->tev[2 * q], c->tev[2 * q + 1]);
+      S.rock_kernel_ms += ms;
+    }
     for (int q = 0; q < na; q++) {
       const int i = act[q];
       Sp& p = sp[i];

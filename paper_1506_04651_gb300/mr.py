@@ -40,7 +40,11 @@ class Stats(C.Structure):
                [("rock_smax", C.c_int32), ("reserved0", C.c_int32), ("rock_rho", C.c_double),
                 ("irregular_rows", C.c_int64), ("irregular_nnz", C.c_int64),
                 ("ms_adapt", C.c_double), ("ms_react", C.c_double), ("ms_diffuse", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64),
+                ("radau_kernel_ms", C.c_double), ("radau_alg_flops", C.c_double),
+                ("radau_kernel_launches", C.c_int64),
+                ("rock_kernel_ms", C.c_double), ("rock_alg_bytes", C.c_double),
+                ("rock_kernel_launches", C.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -78,6 +82,7 @@ def lib():
             "mr_apply_operator": [vp, dp, dp, C.c_int, C.POINTER(C.c_double)],
             "mr_rock4_coefficients": [C.c_int, dp, dp, dp, dp, dp, C.POINTER(C.c_double)],
             "mr_last_error": [vp, C.c_char_p, C.c_size_t],
+            "mr_fp64_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -228,3 +233,12 @@ def rock4_coefficients(s):
 
 def status_str(code):
     return lib().mr_status_str(code).decode()
+
+
+def fp64_fma_rate():
+    """(TFLOP/s, SM MHz) of the device's FP64 FMA pipe, from the library's probe."""
+    t, mhz = C.c_double(), C.c_double()
+    rc = lib().mr_fp64_fma_rate(C.byref(t), C.byref(mhz))
+    if rc:
+        raise MRError(rc, "mr_fp64_fma_rate")
+    return t.value, mhz.value
