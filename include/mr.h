@@ -170,6 +170,39 @@ mr_status mr_apply_operator(mr_ctx *ctx, const double *u_in, double *out, int on
 mr_status mr_rock4_coefficients(int s, double *mu, double *nu, double *kap, double *w,
                                 double *errc, double *ell);
 
+/*
+ * Reaction of a plain array of cells that allocates nothing.  The paper has
+ * no counterpart; this entry point is for callers that cannot allocate device
+ * memory themselves or through a context: code that runs while another
+ * component (a caching allocator, a host application handing out device
+ * pointers) owns the device's memory, or code that must not call into the CUDA
+ * allocator at all.  It integrates u' = f(u) over dt in every cell with the same
+ * Radau5 kernel and control as react_radau5.
+ *   model, params, nparams  as in mr_problem (BZ: m = 3; NAGUMO: m = 1)
+ *   u           device pointer; species i of cell r is u[i*ld + r]; updated in place
+ *   n, ld       number of cells and row stride (0 <= n <= MR_NOALLOC_MAX_CELLS, ld >= n)
+ *   dt, rtol, atol  as in react_radau5 (all > 0)
+ *   complexity  device pointer to n int32 (f evaluations + m per Jacobian), or NULL
+ *   cuda_stream stream the work is ordered on (NULL: legacy default stream); the
+ *               call synchronises it before returning
+ * Scratch: the work-queue head, the status word and the step counters live in a
+ * 512-byte static device array that every GPU which loads this library holds
+ * until the process exits; no cudaMalloc/cudaFree or allocating library call is
+ * made.  The first call on a device looks up that array's device address and
+ * caches it, so make that first call before any stream capture.  All calls share
+ * the array (it keeps the last call's contents; each call clears it first), so
+ * calls whose work overlaps on the GPU -- other streams, other host threads --
+ * race on it and must be serialised by the caller.
+ * Errors: MR_EINVAL for a bad model or parameters, n outside [0,
+ * MR_NOALLOC_MAX_CELLS], ld < n or a NULL u (checked before any GPU work);
+ * MR_ECUDA if the device address of the scratch cannot be obtained or a launch
+ * fails; per-cell Radau5 failures as in react_radau5.
+ */
+#define MR_NOALLOC_MAX_CELLS 2147483647LL
+mr_status mr_react_radau5_noalloc(int model, const double *params, int nparams, double *u,
+                                  int64_t n, int64_t ld, double dt, double rtol, double atol,
+                                  int32_t *complexity, void *cuda_stream);
+
 /* Measurement aid (no counterpart in the paper): FP64 fused multiply-add
  * throughput of the current device in TFLOP/s (2 flops per FMA), from a
  * kernel of independent FMA chains on every SM timed with CUDA events; used

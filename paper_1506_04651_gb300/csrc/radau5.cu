@@ -17,6 +17,7 @@
 // refiltered error estimate after rejections) are the published ones.
 #include <algorithm>
 #include <complex>
+#include <mutex>
 #include <math.h>
 #include <string.h>
 
@@ -713,4 +714,75 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   return (mr_status)c->hc.status;
 }
 
+// ------------------------------------------------------------ no-allocation variant
+// Scratch of mr_react_radau5_noalloc: the work-queue head, status word and
+// counters of one launch (a DevCounters), in a static device array so that the
+// call allocates nothing.  Host code must not use the symbol as an address:
+// its device address is obtained once per device with cudaGetSymbolAddress.
+namespace {
+constexpr int kNoallocScratchBytes = 512;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+static_assert(sizeof(DevCounters) <= kNoallocScratchBytes, "scratch too small for the counters");
+std::mutex g_noalloc_mu;
+constexpr int kNoallocMaxDevices = 256;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+}  // namespace
+
+mr_status react_noalloc(int model, const double* params, int nparams, double* u, int64_t n, int64_t ld,
+                        double dt, double rtol, double atol, int32_t* complexity, cudaStream_t stream) {
+  if (!u || n < 0 || n > MR_NOALLOC_MAX_CELLS || ld < n) return MR_EINVAL;
+  if (!(dt > 0.0) || !(rtol > 0.0) || !(atol > 0.0) || !params) return MR_EINVAL;
+  if (model == MR_MODEL_BZ) {
+    if (nparams < 4 || !(params[0] > 0.0) || !(params[1] > 0.0)) return MR_EINVAL;
+  } else if (model == MR_MODEL_NAGUMO) {
+    if (nparams < 1) return MR_EINVAL;
+  } else {
+    return MR_EINVAL;
+  }
+  if (n == 0) return MR_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return MR_ECUDA;
+  void* addr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MR_ECUDA;
+      g_noalloc_addr[dev] = p;
+    }
+    addr = g_noalloc_addr[dev];
+  }
+  DevCounters* dc = static_cast<DevCounters*>(addr);
+  double rc[64];
+  radau_constants(rc);
+  RadauC C = constants_from(rc);
+  C.rt = 0.1 * pow(rtol, 2.0 / 3.0);
+  C.at = C.rt * (atol / rtol);
+  C.fnewt = std::max(10.0 * 1e-16 / C.rt, std::min(0.03, sqrt(C.rt)));
+  if (cudaMemsetAsync(dc, 0, sizeof(DevCounters), stream) != cudaSuccess) return MR_ECUDA;
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)nsm * 8);
+  if (model == MR_MODEL_BZ) {
+    BZ md{1.0 / params[1], 1.0 / params[0], params[2], params[3]};
+    k_radau<BZ><<<grid, 128, 0, stream>>>(md, C, u, n, ld, dt, complexity, dc);
+  } else {
+    Nagumo md{params[0]};
+    k_radau<Nagumo><<<grid, 128, 0, stream>>>(md, C, u, n, ld, dt, complexity, dc);
+  }
+  if (cudaGetLastError() != cudaSuccess) return MR_ECUDA;
+  int status = 0;
+  if (cudaMemcpyAsync(&status, &dc->status, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return MR_ECUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return MR_ECUDA;
+  return (mr_status)status;
+}
+
 }  // namespace mrg
+
+extern "C" mr_status mr_react_radau5_noalloc(int model, const double* params, int nparams, double* u, int64_t n,
+                                             int64_t ld, double dt, double rtol, double atol,
+                                             int32_t* complexity, void* cuda_stream) {
+  return mrg::react_noalloc(model, params, nparams, u, n, ld, dt, rtol, atol, complexity,
+                            (cudaStream_t)cuda_stream);
+}
