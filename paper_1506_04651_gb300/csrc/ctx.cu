@@ -93,6 +93,11 @@ mr_status alloc_all(mr_ctx* c) {
   A(c->complexity, c->cap_leaves);
   A(c->dc, 1);
   A(c->rho_bits, 1);
+  {
+    double* ctl = nullptr;
+    A(ctl, 1024);  // holds the ROCK4 control block
+    c->rock_ctl = ctl;
+  }
 #undef A
   MR_CUDA(c, cudaMemset(c->dc, 0, sizeof(DevCounters)));
   MR_CUDA(c, cudaMemset(c->complexity, 0, sizeof(int32_t) * c->cap_leaves));
@@ -114,6 +119,8 @@ void free_all(mr_ctx* c) {
   cudaFree(c->rho_bits);
   cudaFree(c->stage[0]);
   cudaFree(c->stage[1]);
+  cudaFree(c->rock_tab);
+  cudaFree(c->rock_ctl);
 }
 
 void refresh_tree_stats(mr_ctx* c) {

@@ -25,6 +25,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "mr_internal.cuh"
 
 namespace mrg {
@@ -433,167 +435,224 @@ __global__ void k_irr_index(const int32_t* __restrict__ irr_flag, const int32_t*
   }
 }
 
+// Merged rows of the leaves at level jumps.  One warp builds one row:
+// the row's faces seed a shared-memory queue of (level, cell, weight) items;
+// every round each lane resolves one item through the direct map -- a leaf
+// adds its weight to the row (shared-memory hash keyed by leaf index), an
+// internal cell pushes its 2^d children with weight / 2^d (projection), an
+// absent cell pushes its parent's 3^d prediction stencil (Eq. inter_1d) --
+// until the queue is empty.  The merged row is sorted by leaf index (so the
+// sums the sweeps take are reproducible run to run) and written to a fixed
+// slot of the row.  Weights are dyadic, so merging is exact in any order.
 template <int D>
-struct RowAcc {
-  static constexpr int kMax = D == 2 ? 96 : 384;
-  int n = 0;
-  bool overflow = false;
-  int32_t col[kMax];
-  double w[kMax];
-  __device__ void add(int32_t c, double v) {
-    for (int q = 0; q < n; q++)
-      if (col[q] == c) {
-        w[q] += v;
-        return;
-      }
-    if (n < kMax) {
-      col[n] = c;
-      w[n] = v;
-      n++;
-    } else {
-      overflow = true;
-    }
-  }
+struct IrrCfg;
+template <>
+struct IrrCfg<2> {
+  static constexpr int kQueue = 256, kHash = 256, kWarps = 4;
+};
+template <>
+struct IrrCfg<3> {
+  static constexpr int kQueue = 8192, kHash = 2048, kWarps = 1;
 };
 
-struct Item {
-  int j;
-  int k[3];
+struct QItem {
   double w;
+  int16_t k[3];
+  int8_t j, pad;
 };
 
-// value of cell (j, k) as a combination of leaf values: leaves directly,
-// internal cells as the mean of their children, absent cells by prediction
 template <int D>
-__device__ void vsym(const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf,
-                     const Level& L, int j0, const int* k0, double w0, RowAcc<D>& acc) {
-  constexpr int kStack = D == 2 ? 96 : 320;
-  Item st[kStack];
-  int sp = 0;
-  st[sp++] = Item{j0, {k0[0], k0[1], k0[2]}, w0};
-  while (sp > 0) {
-    Item it = st[--sp];
-    int k[3] = {0, 0, 0};
-    for (int a = 0; a < D; a++) k[a] = mirror(it.k[a], it.j);
-    int32_t idx = dmap[L.doff[it.j] + morton<D>(k)];
-    if (idx >= 0) {
-      int32_t li = node_leaf[idx];
-      if (li >= 0) {
-        acc.add(li, it.w);
-      } else {
-        for (int t = 0; t < (1 << D); t++) {
-          if (sp >= kStack) {
-            acc.overflow = true;
-            return;
+struct IrrShared {
+  QItem q[IrrCfg<D>::kQueue];
+  int32_t key[IrrCfg<D>::kHash];
+  double val[IrrCfg<D>::kHash];
+  int head, tail, n, bad;
+};
+
+__device__ inline void hash_add(int32_t* key, double* val, int cap, int32_t c, double w, int* bad) {
+  uint32_t s = ((uint32_t)c * 2654435761u) & (cap - 1);
+  for (int probe = 0; probe < cap; probe++) {
+    int32_t old = atomicCAS(&key[s], -1, c);
+    if (old == -1 || old == c) {
+      atomicAdd(&val[s], w);
+      return;
+    }
+    s = (s + 1) & (cap - 1);
+  }
+  atomicExch(bad, 1);
+}
+
+template <int D>
+__device__ inline void qpush(IrrShared<D>& S, int j, const int* k, double w) {
+  int pos = atomicAdd(&S.tail, 1);
+  if (pos - S.head >= IrrCfg<D>::kQueue) {  // head only moves between rounds
+    atomicExch(&S.bad, 1);
+    return;
+  }
+  QItem& it = S.q[pos & (IrrCfg<D>::kQueue - 1)];
+  it.w = w;
+  it.j = (int8_t)j;
+  it.k[0] = (int16_t)k[0];
+  it.k[1] = (int16_t)k[1];
+  it.k[2] = (int16_t)(D == 3 ? k[2] : 0);
+}
+
+template <int D>
+__global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
+    k_irr_rows(const int32_t* __restrict__ irr_leaf, int64_t nrows, const int32_t* __restrict__ leaf_node,
+               const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
+               const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf, Level L, int slot,
+               int32_t* __restrict__ cnt, int32_t* __restrict__ col, double* __restrict__ wout,
+               unsigned long long* rho_bits, DevCounters* dc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kH = IrrCfg<D>::kHash, kQ = IrrCfg<D>::kQueue;
+  IrrShared<D>& S = reinterpret_cast<IrrShared<D>*>(smem_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  for (int64_t row = (int64_t)blockIdx.x * IrrCfg<D>::kWarps + (threadIdx.x >> 5); row < nrows;
+       row += (int64_t)gridDim.x * IrrCfg<D>::kWarps) {
+    for (int q = lane; q < kH; q += 32) {
+      S.key[q] = -1;
+      S.val[q] = 0.0;
+    }
+    if (lane == 0) {
+      S.head = S.tail = S.n = 0;
+      S.bad = 0;
+    }
+    __syncwarp();
+    const int32_t r = irr_leaf[row];
+    const int32_t n = leaf_node[r];
+    const int j = lvl[n];
+    int k[3];
+    unmorton<D>(code[n], k);
+    const int lim = 1 << j;
+    const double ih2 = ldexp(1.0, 2 * j);
+    const double coef = ldexp(1.0, 2 * j + 1 - (D - 1));
+    if (lane < 2 * D) {
+      const int a = lane >> 1, sg = (lane & 1) ? 1 : -1;
+      int q[3] = {k[0], k[1], k[2]};
+      q[a] += sg;
+      if (q[a] >= 0 && q[a] < lim) {  // homogeneous Neumann: no flux through the boundary
+        int32_t idx = dmap[L.doff[j] + morton<D>(q)];
+        if (idx < 0 || node_leaf[idx] >= 0) {
+          qpush<D>(S, j, q, ih2);  // same-level leaf, or ghost by prediction
+          hash_add(S.key, S.val, kH, r, -ih2, &S.bad);
+        } else {
+          // finer side: minus the mean of the fluxes into the touching children
+          for (int t = 0; t < (1 << D); t++) {
+            int c[3] = {0, 0, 0};
+            for (int b = 0; b < D; b++) c[b] = 2 * q[b] + ((t >> b) & 1);
+            if (c[a] != 2 * q[a] + (sg > 0 ? 0 : 1)) continue;
+            int g[3] = {c[0], c[1], c[2]};
+            g[a] -= sg;
+            qpush<D>(S, j + 1, g, -coef);
+            qpush<D>(S, j + 1, c, coef);
           }
-          Item c{it.j + 1, {0, 0, 0}, it.w / (double)(1 << D)};
-          for (int a = 0; a < D; a++) c.k[a] = 2 * k[a] + ((t >> a) & 1);
-          st[sp++] = c;
         }
-      }
-    } else {
-      constexpr int NST = D == 2 ? 9 : 27;
-      for (int o = 0; o < NST; o++) {
-        if (sp >= kStack) {
-          acc.overflow = true;
-          return;
-        }
-        int oo = o;
-        Item c{it.j - 1, {0, 0, 0}, it.w};
-        for (int a = 0; a < D; a++) {
-          int off = oo % 3 - 1;
-          oo /= 3;
-          c.k[a] = (k[a] >> 1) + off;
-          c.w *= wpred(k[a] & 1, off);
-        }
-        st[sp++] = c;
       }
     }
-  }
-}
-
-template <int D>
-__device__ void irregular_row(int32_t r, const int32_t* __restrict__ leaf_node,
-                              const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
-                              const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf,
-                              const Level& L, RowAcc<D>& acc) {
-  int32_t n = leaf_node[r];
-  int j = lvl[n];
-  int k[3];
-  unmorton<D>(code[n], k);
-  const int lim = 1 << j;
-  const double ih2 = ldexp(1.0, 2 * j);
-  const double coef = ldexp(1.0, 2 * j + 1 - (D - 1));
-  for (int f = 0; f < 2 * D; f++) {
-    int a = f >> 1, sg = (f & 1) ? 1 : -1;
-    int q[3] = {k[0], k[1], k[2]};
-    q[a] += sg;
-    if (q[a] < 0 || q[a] >= lim) continue;  // homogeneous Neumann: zero flux
-    int32_t idx = dmap[L.doff[j] + morton<D>(q)];
-    if (idx < 0 || node_leaf[idx] >= 0) {
-      vsym<D>(dmap, node_leaf, L, j, q, ih2, acc);  // same-level leaf or predicted ghost
-      acc.add(r, -ih2);
-    } else {
-      // finer side: minus the mean of the fluxes into the 2^(d-1) touching children
-      for (int t = 0; t < (1 << D); t++) {
+    __syncwarp();
+    for (int round = 0; round < 4096; round++) {
+      const int head = S.head, tail = S.tail;
+      if (head >= tail || S.bad) break;
+      const int mine = head + lane;
+      const bool have = mine < tail;
+      QItem it;
+      if (have) it = S.q[mine & (kQ - 1)];
+      __syncwarp();
+      if (lane == 0) S.head = min(tail, head + 32);
+      __syncwarp();
+      if (have) {
         int c[3] = {0, 0, 0};
-        for (int b = 0; b < D; b++) c[b] = 2 * q[b] + ((t >> b) & 1);
-        if (c[a] != 2 * q[a] + (sg > 0 ? 0 : 1)) continue;
-        int g[3] = {c[0], c[1], c[2]};
-        g[a] -= sg;
-        vsym<D>(dmap, node_leaf, L, j + 1, g, -coef, acc);
-        vsym<D>(dmap, node_leaf, L, j + 1, c, coef, acc);
-      }
-    }
-  }
-}
-
-template <int D>
-__global__ void k_irr_rows(const int32_t* __restrict__ irr_leaf, int64_t nrows,
-                           const int32_t* __restrict__ leaf_node, const uint32_t* __restrict__ code,
-                           const uint8_t* __restrict__ lvl, const int32_t* __restrict__ dmap,
-                           const int32_t* __restrict__ node_leaf, Level L,
-                           int32_t* __restrict__ cnt, const int64_t* __restrict__ ptr,
-                           int32_t* __restrict__ col, double* __restrict__ wout,
-                           unsigned long long* rho_bits, DevCounters* dc) {
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < nrows;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    RowAcc<D> acc;
-    irregular_row<D>(irr_leaf[row], leaf_node, code, lvl, dmap, node_leaf, L, acc);
-    if (acc.overflow) {
-      atomicExch(&dc->overflow, 1);
-      if (cnt) cnt[row] = 0;
-      continue;
-    }
-    // order by column (insertion sort), drop exact zeros
-    for (int a = 1; a < acc.n; a++) {
-      int32_t c = acc.col[a];
-      double w = acc.w[a];
-      int b = a - 1;
-      while (b >= 0 && acc.col[b] > c) {
-        acc.col[b + 1] = acc.col[b];
-        acc.w[b + 1] = acc.w[b];
-        b--;
-      }
-      acc.col[b + 1] = c;
-      acc.w[b + 1] = w;
-    }
-    int nz = 0;
-    double sa = 0.0;
-    for (int a = 0; a < acc.n; a++)
-      if (acc.w[a] != 0.0) {
-        if (!cnt) {
-          col[ptr[row] + nz] = acc.col[a];
-          wout[ptr[row] + nz] = acc.w[a];
+        const int jj = it.j;
+        for (int a = 0; a < D; a++) c[a] = mirror(it.k[a], jj);
+        int32_t idx = dmap[L.doff[jj] + morton<D>(c)];
+        if (idx >= 0) {
+          int32_t li = node_leaf[idx];
+          if (li >= 0) {
+            hash_add(S.key, S.val, kH, li, it.w, &S.bad);
+          } else {
+            const double w = it.w * (1.0 / (1 << D));
+            for (int t = 0; t < (1 << D); t++) {
+              int ch[3] = {0, 0, 0};
+              for (int a = 0; a < D; a++) ch[a] = 2 * c[a] + ((t >> a) & 1);
+              qpush<D>(S, jj + 1, ch, w);
+            }
+          }
+        } else {
+          constexpr int NST = D == 2 ? 9 : 27;
+          for (int o = 0; o < NST; o++) {
+            int oo = o, st[3] = {0, 0, 0};
+            double w = it.w;
+            for (int a = 0; a < D; a++) {
+              int off = oo % 3 - 1;
+              oo /= 3;
+              st[a] = (c[a] >> 1) + off;
+              w *= wpred(c[a] & 1, off);
+            }
+            qpush<D>(S, jj - 1, st, w);
+          }
         }
-        nz++;
-        sa += fabs(acc.w[a]);
       }
-    if (cnt) {
-      cnt[row] = nz;
-    } else {
+      __syncwarp();
+    }
+    __syncwarp();
+    if (S.head < S.tail) S.bad = 1;  // round limit reached
+    // compact the non-zero entries, then sort them by leaf index
+    int32_t* skey = reinterpret_cast<int32_t*>(S.q);  // the queue is free now
+    double* sval = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(S.q) + sizeof(int32_t) * kH);
+    static_assert(sizeof(QItem) * kQ >= (sizeof(int32_t) + sizeof(double)) * kH, "queue too small to sort in");
+    __syncwarp();
+    for (int q = lane; q < kH; q += 32) {
+      if (S.key[q] >= 0 && S.val[q] != 0.0) {
+        int pos = atomicAdd(&S.n, 1);
+        skey[pos] = S.key[q];
+        sval[pos] = S.val[q];
+      }
+    }
+    __syncwarp();
+    const int cntr = S.n;
+    int np2 = 1;
+    while (np2 < cntr) np2 <<= 1;
+    for (int q = cntr + lane; q < np2; q += 32) {
+      skey[q] = 0x7fffffff;
+      sval[q] = 0.0;
+    }
+    __syncwarp();
+    for (int size = 2; size <= np2; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int q = lane; q < np2; q += 32) {
+          int p = q ^ stride;
+          if (p > q) {
+            bool up = (q & size) == 0;
+            if ((skey[q] > skey[p]) == up) {
+              int32_t tk = skey[q];
+              skey[q] = skey[p];
+              skey[p] = tk;
+              double tv = sval[q];
+              sval[q] = sval[p];
+              sval[p] = tv;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    double sa = 0.0;
+    const bool ok = !S.bad && cntr <= slot;
+    for (int q = lane; q < cntr; q += 32) {
+      sa += fabs(sval[q]);
+      if (ok) {
+        col[row * (int64_t)slot + q] = skey[q];
+        wout[row * (int64_t)slot + q] = sval[q];
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    if (lane == 0) {
+      cnt[row] = ok ? cntr : 0;
+      if (!ok) atomicExch(&dc->overflow, 1);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&dc->irr_nnz), (unsigned long long)cntr);
       atomicMax(rho_bits, (unsigned long long)__double_as_longlong(sa));
     }
+    __syncwarp();
   }
 }
 
@@ -840,6 +899,7 @@ mr_status build_tables(mr_ctx* c) {
   Level L = make_level(c, t);
   MR_CUDA(c, cudaMemsetAsync(c->rho_bits, 0, sizeof(unsigned long long), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->overflow, 0, sizeof(int), c->stream));
+  MR_CUDA(c, cudaMemsetAsync(&c->dc->irr_nnz, 0, sizeof(long long), c->stream));
   int32_t* irr_flag = c->itmp;
   if (D == 2)
     k_classify<2><<<grid_for(N), kBlock, 0, c->stream>>>(t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, N,
@@ -853,43 +913,44 @@ mr_status build_tables(mr_ctx* c) {
   c->launches += 2;
   MR_TRY(sync_counts(c));
   const int64_t nrows = c->hc.irr_rows;
+  const int slot = D == 2 ? kIrrSlot2 : kIrrSlot3;
   if (nrows > 0) {
-    if (D == 2)
-      k_irr_rows<2><<<grid_for(nrows, 128), 128, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
-                                                                 t.dmap, t.node_leaf, L, c->irr_cnt, nullptr,
-                                                                 nullptr, nullptr, c->rho_bits, c->dc);
-    else
-      k_irr_rows<3><<<grid_for(nrows, 64), 64, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
-                                                               t.dmap, t.node_leaf, L, c->irr_cnt, nullptr,
-                                                               nullptr, nullptr, c->rho_bits, c->dc);
-    scan_i32_to_i64(c, c->irr_cnt, c->irr_ptr, nrows, &c->dc->irr_nnz);
-    c->launches++;
-    MR_TRY(sync_counts(c));
-    if (c->hc.overflow) {
-      c->last_error = "irregular operator row exceeds its local capacity";
-      return MR_ESTATE;
-    }
-    const int64_t nnz = c->hc.irr_nnz;
-    if (nnz > c->irr_cap) {
+    const int64_t need = nrows * (int64_t)slot;
+    if (need > c->irr_cap) {
       cudaFree(c->irr_col);
       cudaFree(c->irr_w);
-      c->irr_cap = nnz + nnz / 2 + 1024;
+      c->irr_col = nullptr;
+      c->irr_w = nullptr;
+      c->irr_cap = need + need / 2 + 1024;
       MR_CUDA(c, cudaMalloc(&c->irr_col, sizeof(int32_t) * c->irr_cap));
       MR_CUDA(c, cudaMalloc(&c->irr_w, sizeof(double) * c->irr_cap));
     }
-    MR_CUDA(c, cudaMemcpyAsync(c->irr_ptr + nrows, &c->dc->irr_nnz, sizeof(int64_t), cudaMemcpyDeviceToDevice,
-                               c->stream));
-    if (D == 2)
-      k_irr_rows<2><<<grid_for(nrows, 128), 128, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
-                                                                 t.dmap, t.node_leaf, L, nullptr, c->irr_ptr,
-                                                                 c->irr_col, c->irr_w, c->rho_bits, c->dc);
-    else
-      k_irr_rows<3><<<grid_for(nrows, 64), 64, 0, c->stream>>>(c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl,
-                                                               t.dmap, t.node_leaf, L, nullptr, c->irr_ptr,
-                                                               c->irr_col, c->irr_w, c->rho_bits, c->dc);
+    int nsm = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (D == 2) {
+      const size_t sm = sizeof(IrrShared<2>) * IrrCfg<2>::kWarps;
+      MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      int grid = (int)std::min<int64_t>((nrows + IrrCfg<2>::kWarps - 1) / IrrCfg<2>::kWarps, (int64_t)nsm * 16);
+      k_irr_rows<2><<<grid, 32 * IrrCfg<2>::kWarps, sm, c->stream>>>(
+          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, slot, c->irr_cnt, c->irr_col,
+          c->irr_w, c->rho_bits, c->dc);
+    } else {
+      const size_t sm = sizeof(IrrShared<3>) * IrrCfg<3>::kWarps;
+      MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      int grid = (int)std::min<int64_t>((nrows + IrrCfg<3>::kWarps - 1) / IrrCfg<3>::kWarps, (int64_t)nsm * 16);
+      k_irr_rows<3><<<grid, 32 * IrrCfg<3>::kWarps, sm, c->stream>>>(
+          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, slot, c->irr_cnt, c->irr_col,
+          c->irr_w, c->rho_bits, c->dc);
+    }
     c->launches++;
-  } else {
-    c->hc.irr_nnz = 0;
+    MR_CUDA(c, cudaGetLastError());
+  }
+  c->irr_slot = slot;
+  MR_TRY(sync_counts(c));
+  if (c->hc.overflow) {
+    c->last_error = "an operator row at a level jump exceeds its slot";
+    return MR_ESTATE;
   }
   unsigned long long rb = 0;
   MR_CUDA(c, cudaMemcpyAsync(&rb, c->rho_bits, sizeof rb, cudaMemcpyDeviceToHost, c->stream));

@@ -25,6 +25,8 @@ namespace mrg {
 constexpr int kMaxL = MR_MAX_LEVEL;
 constexpr int kMaxM = MR_MAX_SPECIES;
 constexpr int kBlock = 256;
+// merged operator rows at level jumps: entries per row (slot) by dimension
+constexpr int kIrrSlot2 = 128, kIrrSlot3 = 640;
 
 // ---------------------------------------------------------------- Morton codes
 // x is the most significant digit of each group (Sec. 3.1.1).
@@ -138,6 +140,9 @@ struct mr_ctx {
   int32_t* irr_col = nullptr;
   double* irr_w = nullptr;
   int64_t irr_cap = 0;
+  int irr_slot = 0;                  // row stride of irr_col / irr_w
+  double* rock_tab = nullptr;        // ROCK4-type coefficients of every stage count
+  void* rock_ctl = nullptr;          // device control block of the persistent ROCK4 driver
   double rho = 0.0;                  // Gershgorin bound of L
   unsigned long long* rho_bits = nullptr;
   bool tables_valid = false;

@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restr
   constexpr int M = Mdl::M;
   unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (;;) {
-    int cell = atomicAdd(&dc->work_next, 1);
+    const int cell = atomicAdd(&dc->work_next, 1);
     if (cell >= N) break;
     double y[M];
 #pragma unroll
@@ -672,11 +672,18 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   MR_CUDA(c, cudaMemsetAsync(c->dc->radau, 0, sizeof(c->dc->radau), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->work_next, 0, sizeof(int), c->stream));
-  int dev = 0, nsm = 152;
+  // persistent grid: exactly the blocks that are co-resident, each thread
+  // pulling cells from the queue until it is empty
+  int dev = 0, nsm = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (c->prob.model == MR_MODEL_BZ)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radau<BZ>, 128, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radau<Nagumo>, 128, 0);
+  per_sm = std::max(per_sm, 1);
   int64_t want = (N + 127) / 128;
-  int grid = (int)std::min<int64_t>(want, (int64_t)nsm * 8);
+  int grid = (int)std::min<int64_t>(want, (int64_t)nsm * per_sm);
   if (grid < 1) grid = 1;
   MR_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
   if (c->prob.model == MR_MODEL_BZ) {

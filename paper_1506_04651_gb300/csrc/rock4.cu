@@ -18,6 +18,7 @@
 // 5/7-point weights 1/h_j^2; the few leaves at level jumps use a
 // precomputed merged row of (leaf, weight) pairs.  The error norm is a
 // deterministic two-pass reduction.
+#include <cooperative_groups.h>
 #include <math.h>
 #include <string.h>
 
@@ -51,10 +52,16 @@ struct StageArgs {
 
 __constant__ double c_ih2[kMaxL + 1];
 
+struct IrrRows {
+  const int32_t* cnt;
+  const int32_t* col;
+  const double* w;
+  int slot;
+};
+
 template <int D>
 __device__ inline double apply_L(const double* __restrict__ x, int64_t r, const int32_t* __restrict__ nbr,
-                                 int64_t capL, int32_t n0, double ih2, const int64_t* __restrict__ irr_ptr,
-                                 const int32_t* __restrict__ irr_col, const double* __restrict__ irr_w) {
+                                 int64_t capL, int32_t n0, double ih2, const IrrRows& R) {
   if (n0 >= 0) {
     double s = x[n0];
 #pragma unroll
@@ -62,17 +69,18 @@ __device__ inline double apply_L(const double* __restrict__ x, int64_t r, const 
     return (s - 2.0 * D * x[r]) * ih2;
   }
   const int64_t row = -(int64_t)n0 - 1;
+  const int32_t* col = R.col + row * R.slot;
+  const double* w = R.w + row * R.slot;
+  const int n = R.cnt[row];
   double s = 0.0;
-  for (int64_t e = irr_ptr[row]; e < irr_ptr[row + 1]; e++) s += irr_w[e] * x[irr_col[e]];
+  for (int e = 0; e < n; e++) s += w[e] * x[col[e]];
   return s;
 }
 
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_rock(StageArgs A, int64_t N, int64_t capL,
                                                  const int32_t* __restrict__ nbr, const uint8_t* __restrict__ lvl,
-                                                 const int64_t* __restrict__ irr_ptr,
-                                                 const int32_t* __restrict__ irr_col,
-                                                 const double* __restrict__ irr_w, double* __restrict__ red) {
+                                                 IrrRows R, double* __restrict__ red) {
   __shared__ double sh[kBlock];
   double errs[kMaxM];
   for (int i = 0; i < A.nspec; i++) errs[i] = 0.0;
@@ -81,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_rock(StageArgs A, int64_t N, int64_t
     const double ih2 = c_ih2[lvl[r]];
     for (int i = 0; i < A.nspec; i++) {
       const SpecOp& o = A.op[i];
-      double Lx = apply_L<D>(o.x, r, nbr, capL, n0, ih2, irr_ptr, irr_col, irr_w);
+      double Lx = apply_L<D>(o.x, r, nbr, capL, n0, ih2, R);
       switch (A.mode) {
         case M_STAGE:
           o.out[r] = o.ca * o.a[r] + (o.b ? o.cb * o.b[r] : 0.0) + o.cl * Lx;
@@ -123,20 +131,359 @@ __global__ void __launch_bounds__(kBlock) k_rock(StageArgs A, int64_t N, int64_t
   }
 }
 
-__global__ void k_reduce_rows(const double* __restrict__ red, int nb, int nspec, double* __restrict__ out) {
-  __shared__ double sh[kBlock];
-  for (int i = 0; i < nspec; i++) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += red[i * nb + b];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = kBlock / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-      __syncthreads();
+// ------------------------------------------------------------ persistent driver
+// One cooperative launch integrates a whole diffusion sub-step D_dt for every
+// species: ROCK4 steps are taken, accepted or rejected and resized on the
+// device, with grid-wide barriers between sweeps (the vectors of the
+// benchmark's grids are L2-resident, so a barrier is far cheaper than a kernel
+// launch and a host round trip per step).  Block 0, thread 0 runs the control
+// of every species with the host driver's arithmetic; everything else is the
+// same per-leaf sweep as k_rock.
+
+// coefficient table for s = 5..152: [l_s, w0..w4, e0..e3, mu_1..n, nu_1..n, kap_1..n]
+struct RockTab {
+  const double* data;
+  int off[kSmax + 1];
+};
+
+struct RockCtl {
+  double t[kMaxM], h[kMaxM], err[kMaxM];
+  int done[kMaxM], last[kMaxM], s[kMaxM], n[kMaxM], a[kMaxM], acc_prev[kMaxM], c_prev[kMaxM];
+  int nmax, finished, status, rounds;
+  long long steps, rejects, stages, matvecs;
+  int smax;
+  double bytes;
+};
+
+struct PersArgs {
+  int m, D, nb;
+  int64_t N, capL;
+  double dt, tol, rho;
+  double Dc[kMaxM];
+  double* U;
+  double* W[4];
+  double* part;  // [kMaxM][nb]
+  RockCtl* ctl;
+  RockTab tab;
+};
+
+__device__ inline double ell_dev(int s) { return 0.336 * (double)s * s - 2.7; }
+
+// control section (one thread): choose the next step of every species
+__device__ void rock_prepare(const PersArgs& P, RockCtl& C, int64_t N, double leafb) {
+  int nmax = 0, any = 0;
+  double bytes = 0.0;
+  for (int i = 0; i < P.m; i++) {
+    if (C.done[i]) continue;
+    if (C.h[i] <= 1e-14 * P.dt) {
+      C.status = MR_EROCK_STEP;
+      C.finished = 1;
+      return;
     }
-    if (threadIdx.x == 0) out[i] = sh[0];
-    __syncthreads();
+    const double rho = P.Dc[i] * P.rho;
+    C.last[i] = 0;
+    if (C.t[i] + 1.0001 * C.h[i] >= P.dt) {
+      C.h[i] = P.dt - C.t[i];
+      C.last[i] = 1;
+    }
+    int s = kSmax;
+    for (int q = kSmin; q <= kSmax; q++)
+      if (ell_dev(q) >= rho * C.h[i]) {
+        s = q;
+        break;
+      }
+    if (ell_dev(s) < rho * C.h[i]) {
+      C.h[i] = ell_dev(kSmax) / rho;
+      C.last[i] = 0;
+    }
+    C.s[i] = s;
+    C.n[i] = s - 4;
+    C.a[i] = (s - 5) % 3;
+    nmax = max(nmax, s - 4);
+    C.steps++;
+    C.stages += s;
+    C.smax = max(C.smax, s);
+    C.matvecs += s + 1;
+    // sweep bytes: stages 16/24, Horner 16+24+32+40, FSAL 24
+    bytes += N * (16.0 + 24.0 * (s - 5) + 112.0 + 24.0);
+    any = 1;
   }
+  C.nmax = nmax;
+  C.bytes += bytes + (double)(nmax + 5) * leafb;
+  if (!any) C.finished = 1;
+}
+
+// operands of one species in one sweep of the persistent driver
+enum { K_STAGE = 0, K_H3, K_H2, K_H1, K_H0, K_FSAL };
+constexpr int kPhaseFinish = 1000;  // phases 1..n: stages; kPhaseFinish + K_*: finishing sweeps
+
+struct Ops {
+  const double *x, *a, *b;
+  double *out, *acc;
+  double ca, cb, cl, e0, e1, e2;
+  int kind;
+};
+
+__device__ inline void combine(const Ops& o, int64_t r, double Lx, const double* yn, double tol, double& err) {
+  switch (o.kind) {
+    case K_STAGE:
+      o.out[r] = o.ca * o.a[r] + (o.b ? o.cb * o.b[r] : 0.0) + o.cl * Lx;
+      break;
+    case K_H3:
+    case K_H2:
+      o.out[r] = o.ca * o.a[r] + o.cl * Lx;
+      break;
+    case K_H1: {
+      const double v = o.ca * o.a[r] + o.cl * Lx;  // h1 = w1 yP + z h2
+      o.out[r] = v;
+      o.acc[r] = o.e0 * o.a[r] + o.e1 * v + o.e2 * o.x[r];
+      break;
+    }
+    case K_H0: {
+      const double v = o.a[r] + o.cl * Lx;  // y_{n+1} = yP + z h1
+      o.out[r] = v;
+      o.acc[r] += v;
+      break;
+    }
+    default: {  // embedded estimate e = acc + d z y_{n+1}
+      const double ee = o.acc[r] + o.cl * Lx;
+      const double sc = tol + tol * fmax(fabs(yn[r]), fabs(o.x[r]));
+      err += (ee / sc) * (ee / sc);
+    }
+  }
+}
+
+template <int D, int M>
+__global__ void __launch_bounds__(kBlock) k_rock_persistent(PersArgs P, const int32_t* __restrict__ nbr,
+                                                            const uint8_t* __restrict__ lvl, IrrRows R,
+                                                            const int32_t* __restrict__ irr_leaf, int64_t nirr) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[kBlock];
+  // per-block copy of the control fields the sweeps read, refreshed after each
+  // control section with loads that bypass L1
+  __shared__ int s_done[kMaxM], s_n[kMaxM], s_s[kMaxM], s_a[kMaxM], s_acc[kMaxM], s_cp[kMaxM];
+  __shared__ double s_h[kMaxM];
+  __shared__ int s_nmax, s_fin;
+  RockCtl& C = *P.ctl;
+  const int64_t N = P.N, capL = P.capL;
+  auto refresh = [&]() {
+    if (threadIdx.x < M) {
+      const int i = threadIdx.x;
+      s_done[i] = __ldcg(&C.done[i]);
+      s_n[i] = __ldcg(&C.n[i]);
+      s_s[i] = __ldcg(&C.s[i]);
+      s_a[i] = __ldcg(&C.a[i]);
+      s_acc[i] = __ldcg(&C.acc_prev[i]);
+      s_cp[i] = __ldcg(&C.c_prev[i]);
+      s_h[i] = __ldcg(&C.h[i]);
+    }
+    if (threadIdx.x == 0) {
+      s_nmax = __ldcg(&C.nmax);
+      s_fin = __ldcg(&C.finished);
+    }
+    __syncthreads();
+  };
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const double leafb = N * (8.0 * D + 1.0);
+  auto Wp = [&](int q, int i) { return P.W[q] + (int64_t)i * capL; };
+  auto Up = [&](int i) { return P.U + (int64_t)i * capL; };
+  // operands of species i in `phase`, built once per sweep; false if the
+  // species sits this sweep out
+  auto ops_for = [&](int phase, int i, Ops& o) -> bool {
+    if (s_done[i]) return false;
+    const double* tb = P.tab.data + P.tab.off[s_s[i]];
+    const double hd = s_h[i] * P.Dc[i];
+    o.b = nullptr;
+    o.acc = nullptr;
+    if (phase < kPhaseFinish) {
+      const int j = phase, n = s_n[i];
+      if (j > n) return false;
+      o.kind = K_STAGE;
+      o.x = j == 1 ? Up(i) : Wp((j - 2) % 3, i);
+      o.a = o.x;
+      o.b = j == 1 ? nullptr : (j == 2 ? Up(i) : Wp((j - 3) % 3, i));
+      o.out = Wp((j - 1) % 3, i);
+      o.ca = tb[10 + (j - 1)];
+      o.cb = tb[10 + n + (j - 1)];
+      o.cl = tb[10 + 2 * n + (j - 1)] * s_h[i] * P.Dc[i];
+      return true;
+    }
+    const double* w = tb + 1;
+    const double* e = tb + 6;
+    const int a = s_a[i], b = (a + 1) % 3, cc = (a + 2) % 3;
+    o.kind = phase - kPhaseFinish;
+    switch (o.kind) {
+      case K_H3: o.x = Wp(a, i); o.a = Wp(a, i); o.out = Wp(b, i); o.ca = w[3]; o.cl = w[4] * hd; break;
+      case K_H2: o.x = Wp(b, i); o.a = Wp(a, i); o.out = Wp(cc, i); o.ca = w[2]; o.cl = hd; break;
+      case K_H1:
+        o.x = Wp(cc, i); o.a = Wp(a, i); o.out = Wp(b, i); o.acc = Wp(3, i); o.ca = w[1]; o.cl = hd;
+        o.e0 = e[0]; o.e1 = e[1]; o.e2 = e[2];
+        break;
+      case K_H0: o.x = Wp(b, i); o.a = Wp(a, i); o.out = Wp(cc, i); o.acc = Wp(3, i); o.ca = 1.0; o.cl = hd; break;
+      default: o.x = Wp(cc, i); o.a = nullptr; o.out = nullptr; o.acc = Wp(3, i); o.cl = e[3] * hd;
+    }
+    return true;
+  };
+  // one sweep: regular leaves one thread each (neighbour indices loaded once
+  // for all species), merged rows one warp each
+  __shared__ Ops s_ops[M];
+  __shared__ int s_act[M];
+  auto sweep = [&](int phase, double* err) {
+    // operands of every species, built once per sweep per block; read from
+    // shared memory so that they do not hold registers across the loops
+    __syncthreads();
+    if (threadIdx.x < M) s_act[threadIdx.x] = ops_for(phase, threadIdx.x, s_ops[threadIdx.x]);
+    __syncthreads();
+    const Ops* o = s_ops;
+    const int* act = s_act;
+    for (int64_t r = tid; r < N; r += nth) {
+      const int32_t n0 = nbr[r];
+      if (n0 < 0) continue;
+      int32_t nb[2 * D];
+      nb[0] = n0;
+#pragma unroll
+      for (int f = 1; f < 2 * D; f++) nb[f] = nbr[f * capL + r];
+      const double ih2 = c_ih2[lvl[r]];
+#pragma unroll
+      for (int i = 0; i < M; i++) {
+        if (!act[i]) continue;
+        const double* x = o[i].x;
+        double sx = x[nb[0]];
+#pragma unroll
+        for (int f = 1; f < 2 * D; f++) sx += x[nb[f]];
+        combine(o[i], r, (sx - 2.0 * D * x[r]) * ih2, Up(i), P.tol, err[i]);
+      }
+    }
+    // merged rows: 8 lanes per row, four rows per warp in flight; each entry's
+    // loads are issued for every species at once
+    constexpr int G = 8;
+    const int sub = lane & (G - 1);
+    const int64_t grp = (tid >> 3), ngrp = nth >> 3;
+    const int64_t rounds = (nirr + ngrp - 1) / ngrp;
+    for (int64_t k = 0; k < rounds; k++) {
+      const int64_t row = grp + k * ngrp;
+      const bool have = row < nirr;
+      double v[M];
+#pragma unroll
+      for (int i = 0; i < M; i++) v[i] = 0.0;
+      int32_t r = 0;
+      if (have) {
+        r = irr_leaf[row];
+        const int cnt = R.cnt[row];
+        const int32_t* col = R.col + row * (int64_t)R.slot;
+        const double* wr = R.w + row * (int64_t)R.slot;
+#pragma unroll 4
+        for (int e = sub; e < cnt; e += G) {
+          const int32_t cidx = col[e];
+          const double we = wr[e];
+#pragma unroll
+          for (int i = 0; i < M; i++)
+            if (act[i]) v[i] += we * o[i].x[cidx];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < M; i++)
+        for (int sft = G / 2; sft > 0; sft >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], sft);
+      if (have && sub == 0) {
+#pragma unroll
+        for (int i = 0; i < M; i++)
+          if (act[i]) combine(o[i], r, v[i], Up(i), P.tol, err[i]);
+      }
+    }
+  };
+  if (tid == 0) {
+    rock_prepare(P, C, N, leafb);
+    __threadfence();
+  }
+  grid.sync();
+  refresh();
+  for (int round = 0; round < 20000; round++) {
+    if (s_fin) break;
+    const int nmax = s_nmax;
+    double err[M];
+#pragma unroll
+    for (int i = 0; i < M; i++) err[i] = 0.0;
+    // recurrence stages P_j -> W[(j-1) % 3]
+    for (int j = 1; j <= nmax; j++) {
+      sweep(j, err);
+      grid.sync();
+    }
+    // Horner finishing procedure and the embedded estimate
+    for (int mode = K_H3; mode <= K_FSAL; mode++) {
+      sweep(kPhaseFinish + mode, err);
+      if (mode == K_FSAL) {
+#pragma unroll
+        for (int i = 0; i < M; i++) {
+          if (s_done[i]) continue;  // uniform across the grid
+          sh[threadIdx.x] = err[i];
+          __syncthreads();
+          for (int w = kBlock / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+          }
+          if (threadIdx.x == 0) P.part[i * P.nb + blockIdx.x] = sh[0];
+          __syncthreads();
+        }
+      }
+      grid.sync();
+    }
+    // control: block 0 reduces the per-block partial sums in a fixed order
+    // (strided by thread, then a tree), thread 0 accepts / rejects and sizes
+    // the next steps
+    __shared__ double s_err2[kMaxM];
+    if (blockIdx.x == 0) {
+      for (int i = 0; i < M; i++) {
+        if (s_done[i]) continue;
+        double v = 0.0;
+        for (int b = threadIdx.x; b < P.nb; b += blockDim.x) v += __ldcg(&P.part[i * P.nb + b]);
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int w = kBlock / 2; w > 0; w >>= 1) {
+          if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+          __syncthreads();
+        }
+        if (threadIdx.x == 0) s_err2[i] = sh[0];
+        __syncthreads();
+      }
+    }
+    if (tid == 0) {
+      for (int i = 0; i < M; i++) {
+        C.acc_prev[i] = 0;
+        if (C.done[i]) continue;
+        const double s2 = s_err2[i];
+        const double err = sqrt(s2 / (double)N);
+        C.err[i] = err;
+        if (!isfinite(err)) {
+          C.status = MR_ENONFINITE;
+          C.finished = 1;
+          break;
+        }
+        const double fac = err == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.8 * pow(err, -0.25)));
+        if (err <= 1.0) {
+          C.acc_prev[i] = 1;
+          C.c_prev[i] = (C.a[i] + 2) % 3;
+          C.t[i] = C.last[i] ? P.dt : C.t[i] + C.h[i];
+          if (C.last[i]) C.done[i] = 1;
+        } else {
+          C.rejects++;
+        }
+        C.h[i] *= fac;
+      }
+      C.rounds++;
+      if (!C.finished) rock_prepare(P, C, N, leafb);
+      __threadfence();
+    }
+    grid.sync();
+    refresh();
+    // accepted species: the new state replaces the old
+    for (int64_t r = tid; r < N; r += nth)
+      for (int i = 0; i < M; i++)
+        if (s_acc[i]) Up(i)[r] = Wp(s_cp[i], i)[r];
+    grid.sync();
+  }
+  if (tid == 0 && !s_fin) C.status = MR_EROCK_STEP;
 }
 
 // ------------------------------------------------------------ host coefficients
@@ -316,12 +663,11 @@ static double sweep_bytes(const mr_ctx* c, const StageArgs& A, int64_t N) {
 
 static void launch_rock(mr_ctx* c, const StageArgs& A, int64_t N, int nb, int* nev = nullptr) {
   if (nev && *nev < 256) cudaEventRecord(c->tev[2 * *nev], c->stream);
+  IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_slot};
   if (c->d == 2)
-    k_rock<2><<<nb, kBlock, 0, c->stream>>>(A, N, c->cap_leaves, c->nbr, c->leaf_lvl, c->irr_ptr, c->irr_col,
-                                            c->irr_w, c->red);
+    k_rock<2><<<nb, kBlock, 0, c->stream>>>(A, N, c->cap_leaves, c->nbr, c->leaf_lvl, R, c->red);
   else
-    k_rock<3><<<nb, kBlock, 0, c->stream>>>(A, N, c->cap_leaves, c->nbr, c->leaf_lvl, c->irr_ptr, c->irr_col,
-                                            c->irr_w, c->red);
+    k_rock<3><<<nb, kBlock, 0, c->stream>>>(A, N, c->cap_leaves, c->nbr, c->leaf_lvl, R, c->red);
   c->launches++;
   if (nev && *nev < 256) {
     cudaEventRecord(c->tev[2 * *nev + 1], c->stream);
@@ -354,157 +700,111 @@ mr_status apply_operator(mr_ctx* c, const double* in, double* out) {
   return MR_OK;
 }
 
+// device coefficient table for every s (built once per process on the host)
+static const double* device_table(mr_ctx* c, RockTab* tab) {
+  static std::vector<double> host;
+  static int off[kSmax + 1];
+  if (host.empty()) {
+    for (int s = kSmin; s <= kSmax; s++) {
+      const Coeffs* C = get_coeffs(s);
+      if (!C) return nullptr;
+      off[s] = (int)host.size();
+      const int n = s - 4;
+      host.push_back(C->ell);
+      for (int k = 0; k < 5; k++) host.push_back(C->w[k]);
+      for (int k = 0; k < 4; k++) host.push_back(C->errc[k]);
+      for (int j = 1; j <= n; j++) host.push_back(C->mu[j]);
+      for (int j = 1; j <= n; j++) host.push_back(C->nu[j]);
+      for (int j = 1; j <= n; j++) host.push_back(C->kap[j]);
+    }
+  }
+  if (!c->rock_tab) {
+    if (cudaMalloc(&c->rock_tab, sizeof(double) * host.size()) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(c->rock_tab, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return nullptr;
+  }
+  for (int s = 0; s <= kSmax; s++) tab->off[s] = s >= kSmin ? off[s] : 0;
+  tab->data = c->rock_tab;
+  return c->rock_tab;
+}
+
 mr_status diffuse(mr_ctx* c, double dt, double tol) {
   mr_status st = build_tables(c);
   if (st) return st;
   const int m = c->m;
-  const int64_t N = c->tb[c->cur].nleaves, cap = c->cap_leaves;
+  const int64_t N = c->tb[c->cur].nleaves;
   double ih2[kMaxL + 1];
   for (int j = 0; j <= kMaxL; j++) ih2[j] = ldexp(1.0, 2 * j);
   MR_CUDA(c, cudaMemcpyToSymbolAsync(c_ih2, ih2, sizeof ih2, 0, cudaMemcpyHostToDevice, c->stream));
-  double* U = c->tb[c->cur].U;
-  const int nb = std::max(1, std::min(grid_for(N), 152 * 8));
-  struct Sp {
-    double t = 0, h = 0, rho = 0;
-    bool done = false, last = false;
-    const Coeffs* C = nullptr;
-    int n = 0, a = 0;
-  } sp[kMaxM];
+  PersArgs P;
+  memset(&P, 0, sizeof P);
+  if (!device_table(c, &P.tab)) {
+    c->last_error = "ROCK4 coefficient table";
+    return MR_ESTATE;
+  }
+  int dev = 0, nsm = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (m != 1 && m != 3) {
+    c->last_error = "diffusion is built for 1 or 3 species";
+    return MR_EINVAL;
+  }
+  const void* kern = c->d == 2 ? (m == 3 ? (const void*)k_rock_persistent<2, 3> : (const void*)k_rock_persistent<2, 1>)
+                               : (m == 3 ? (const void*)k_rock_persistent<3, 3> : (const void*)k_rock_persistent<3, 1>);
+  MR_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+  if (per_sm < 1) return MR_ECUDA;
+  // enough blocks to cover the leaves, at most what is co-resident
+  const int64_t want = std::max<int64_t>(1, (N + kBlock - 1) / kBlock);
+  // enough blocks to cover the leaves, at most two co-resident per SM
+  const int nb = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 2));
+  RockCtl hctl;
+  memset(&hctl, 0, sizeof hctl);
   for (int i = 0; i < m; i++) {
-    sp[i].h = dt;
-    sp[i].rho = c->prob.D[i] * c->rho;
-    sp[i].done = !(dt > 0.0) || c->prob.D[i] == 0.0 || N == 0;
+    hctl.h[i] = dt;
+    hctl.done[i] = !(dt > 0.0) || c->prob.D[i] == 0.0 || N == 0;
   }
-  mr_stats& S = c->stats;
-  S.rock_steps = S.rock_reject = S.rock_stages = S.rock_matvec = 0;
-  S.rock_smax = 0;
-  auto W = [&](int q, int i) { return c->work[q] + (int64_t)i * cap; };
-  for (int round = 0;; round++) {
-    int act[kMaxM], na = 0, nmax = 0, nev = 0;
-    for (int i = 0; i < m; i++) {
-      if (sp[i].done) continue;
-      Sp& p = sp[i];
-      if (p.h <= 1e-14 * dt) {
-        c->last_error = "ROCK4 step size underflow";
-        return MR_EROCK_STEP;
-      }
-      p.last = false;
-      if (p.t + 1.0001 * p.h >= dt) {
-        p.h = dt - p.t;
-        p.last = true;
-      }
-      int s = kSmax;
-      for (int q = kSmin; q <= kSmax; q++)
-        if (rock4_ell(q) >= p.rho * p.h) {
-          s = q;
-          break;
-        }
-      if (rock4_ell(s) < p.rho * p.h) {
-        p.h = rock4_ell(kSmax) / p.rho;
-        p.last = false;
-      }
-      p.C = get_coeffs(s);
-      if (!p.C) return MR_ESTATE;
-      p.n = s - 4;
-      p.a = (p.n - 1) % 3;
-      nmax = std::max(nmax, p.n);
-      S.rock_steps++;
-      S.rock_stages += s;
-      S.rock_smax = std::max(S.rock_smax, s);
-      act[na++] = i;
-    }
-    if (na == 0) break;
-    if (round > 100000) return MR_EROCK_STEP;
-    // recurrence stages: P_j -> W[(j-1) % 3]
-    for (int j = 1; j <= nmax; j++) {
-      StageArgs A;
-      memset(&A, 0, sizeof A);
-      A.mode = M_STAGE;
-      A.D = c->d;
-      for (int q = 0; q < na; q++) {
-        Sp& p = sp[act[q]];
-        if (j > p.n) continue;
-        const int i = act[q];
-        SpecOp& o = A.op[A.nspec++];
-        const double hd = p.h * c->prob.D[i];
-        o.x = j == 1 ? U + (int64_t)i * cap : W((j - 2) % 3, i);
-        o.a = o.x;
-        o.b = j == 1 ? nullptr : (j == 2 ? U + (int64_t)i * cap : W((j - 3) % 3, i));
-        o.out = W((j - 1) % 3, i);
-        o.ca = p.C->mu[j];
-        o.cb = p.C->nu[j];
-        o.cl = p.C->kap[j] * hd;
-        S.rock_matvec++;
-      }
-      launch_rock(c, A, N, nb, &nev);
-    }
-    // Horner steps and the error estimate
-    for (int mode = M_H3; mode <= M_FSAL; mode++) {
-      StageArgs A;
-      memset(&A, 0, sizeof A);
-      A.mode = mode;
-      A.D = c->d;
-      for (int q = 0; q < na; q++) {
-        Sp& p = sp[act[q]];
-        const int i = act[q];
-        const int a = p.a, b = (p.a + 1) % 3, cc = (p.a + 2) % 3;
-        const double hd = p.h * c->prob.D[i];
-        const double* w = p.C->w;
-        SpecOp& o = A.op[A.nspec++];
-        o.tol = tol;
-        switch (mode) {
-          case M_H3:  // h3 = w3 yP + w4 z yP
-            o.x = W(a, i); o.a = W(a, i); o.out = W(b, i); o.ca = w[3]; o.cl = w[4] * hd;
-            break;
-          case M_H2:  // h2 = w2 yP + z h3
-            o.x = W(b, i); o.a = W(a, i); o.out = W(cc, i); o.ca = w[2]; o.cl = hd;
-            break;
-          case M_H1:  // h1 = w1 yP + z h2 ; acc = e0 yP + e1 h1 + e2 h2
-            o.x = W(cc, i); o.a = W(a, i); o.out = W(b, i); o.acc = W(3, i); o.ca = w[1]; o.cl = hd;
-            o.e0 = p.C->errc[0]; o.e1 = p.C->errc[1]; o.e2 = p.C->errc[2];
-            break;
-          case M_H0:  // y1 = yP + z h1 ; acc += y1
-            o.x = W(b, i); o.a = W(a, i); o.out = W(cc, i); o.acc = W(3, i); o.cl = hd;
-            break;
-          default:  // e = acc + d z y1
-            o.x = W(cc, i); o.acc = W(3, i); o.yn = U + (int64_t)i * cap; o.cl = p.C->errc[3] * hd;
-        }
-        S.rock_matvec++;
-      }
-      launch_rock(c, A, N, nb, &nev);
-    }
-    k_reduce_rows<<<1, kBlock, 0, c->stream>>>(c->red, nb, na, c->red_out);
-    c->launches++;
-    double err2[kMaxM];
-    MR_CUDA(c, cudaMemcpyAsync(err2, c->red_out, sizeof(double) * na, cudaMemcpyDeviceToHost, c->stream));
-    MR_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int q = 0; q < nev; q++) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, c->tev[2 * q], c->tev[2 * q + 1]);
-      S.rock_kernel_ms += ms;
-    }
-    for (int q = 0; q < na; q++) {
-      const int i = act[q];
-      Sp& p = sp[i];
-      double err = sqrt(err2[q] / (double)N);
-      if (!isfinite(err)) {
-        c->last_error = "non-finite ROCK4 error estimate";
-        return MR_ENONFINITE;
-      }
-      double fac = err == 0.0 ? 2.0 : std::min(2.0, std::max(0.2, 0.8 * pow(err, -0.25)));
-      if (err <= 1.0) {
-        MR_CUDA(c, cudaMemcpyAsync(U + (int64_t)i * cap, W((p.a + 2) % 3, i), sizeof(double) * N,
-                                   cudaMemcpyDeviceToDevice, c->stream));
-        p.t = p.last ? dt : p.t + p.h;
-        if (p.last) p.done = true;
-      } else {
-        S.rock_reject++;
-      }
-      p.h *= fac;
-    }
-  }
-  MR_CUDA(c, cudaGetLastError());
+  RockCtl* dctl = reinterpret_cast<RockCtl*>(c->rock_ctl);
+  MR_CUDA(c, cudaMemcpyAsync(dctl, &hctl, sizeof hctl, cudaMemcpyHostToDevice, c->stream));
+  P.m = m;
+  P.D = c->d;
+  P.nb = nb;
+  P.N = N;
+  P.capL = c->cap_leaves;
+  P.dt = dt;
+  P.tol = tol;
+  P.rho = c->rho;
+  for (int i = 0; i < m; i++) P.Dc[i] = c->prob.D[i];
+  P.U = c->tb[c->cur].U;
+  for (int q = 0; q < 4; q++) P.W[q] = c->work[q];
+  P.part = c->red;
+  P.ctl = dctl;
+  IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_slot};
+  const int32_t* nbr = c->nbr;
+  const uint8_t* lvl = c->leaf_lvl;
+  const int32_t* irr_leaf = c->irr_leaf;
+  int64_t nirr = c->stats.irregular_rows;
+  void* args[] = {&P, (void*)&nbr, (void*)&lvl, &R, (void*)&irr_leaf, &nirr};
+  MR_CUDA(c, cudaEventRecord(c->tev[0], c->stream));
+  MR_CUDA(c, cudaLaunchCooperativeKernel(kern, nb, kBlock, args, 0, c->stream));
+  MR_CUDA(c, cudaEventRecord(c->tev[1], c->stream));
+  c->launches++;
+  MR_CUDA(c, cudaMemcpyAsync(&hctl, dctl, sizeof hctl, cudaMemcpyDeviceToHost, c->stream));
   MR_CUDA(c, cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]);
+  mr_stats& S = c->stats;
+  S.rock_steps = hctl.steps;
+  S.rock_reject = hctl.rejects;
+  S.rock_stages = hctl.stages;
+  S.rock_matvec = hctl.matvecs;
+  S.rock_smax = hctl.smax;
+  S.rock_kernel_ms += ms;
+  S.rock_kernel_launches++;
+  S.rock_alg_bytes += hctl.bytes + 12.0 * S.irregular_nnz * 0.0;
+  if (hctl.status) {
+    c->last_error = "ROCK4 step control failed";
+    return (mr_status)hctl.status;
+  }
   return MR_OK;
 }
 

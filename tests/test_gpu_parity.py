@@ -85,7 +85,7 @@ def test_adapt_after_reaction_matches_oracle_exactly(mr, J, gen, eta):
     assert np.array_equal(v_o, v_g)
 
 
-@pytest.mark.parametrize("d,J", [(2, 8), (2, 10), (3, 5)])
+@pytest.mark.parametrize("d,J", [(2, 8), (2, 10), (3, 5), (3, 6)])
 def test_operator_matches_oracle(mr, d, J):
     u0 = I.bz_cross_2d(J, 2) if d == 2 else I.bz_sphere_3d(J, 3)
     T = oracle_tree(d, J, u0, 1e-3)
