@@ -37,9 +37,10 @@ METRIC = "leaf-cell Strang updates/s on 1 GB300, mixed vs FP64 at rel-L1 ≤1e-5
 UNIT = "leaf-updates/s"
 
 WORKLOADS = {
-    "bz2d_J10_eta1e-3": dict(d=2, J=10, eta=1e-3, dt=1e-3, gen="cross", seed=2,
+    "bz2d_J10_eta1e-3": dict(d=2, J=10, eta=1e-3, dt=1e-3, gen="cross", seed=2, w=0.01, amp=0.1,
                              desc="2D BZ, J=10 (1024^2 finest), eta=1e-3, graded, two crossing "
-                                  "tanh fronts (w=0.02) + smooth seeded noise, dt=1e-3, FP64"),
+                                  "tanh fronts (w=0.01) with smooth seeded position noise (8 modes, "
+                                  "amplitude 0.1): ~10% of finest cells are leaves; dt=1e-3, FP64"),
     "bz2d_J7_uniform": dict(d=2, J=7, eta=0.0, dt=1e-3, gen="front", seed=1,
                             desc="2D BZ, uniform 128^2 (J=7, eta=0), tanh front + 1% seeded noise, "
                                  "dt=1e-3, FP64"),
@@ -47,6 +48,11 @@ WORKLOADS = {
                             desc="3D BZ, J=7 (128^3 finest), eta=1e-2, spherical front r=0.3, "
                                  "w=0.02 + smooth seeded noise, dt=1e-3, FP64"),
 }
+BATCH = {"batch64_bz2d": dict(n=64, dt=1e-3,
+                              desc="64 independent 2D BZ instances, seeded J ~ U{7..10}, f ~ U[0.9, 2.0], "
+                                   "eta log-uniform in [1e-4, 1e-2], front position ~ U[0.2, 0.8] "
+                                   "(master seed 2026); one context and CUDA stream per instance, "
+                                   "driven concurrently by host threads; FP64")}
 DEFAULT = "bz2d_J10_eta1e-3"
 TOL = 1e-6
 
@@ -54,10 +60,27 @@ TOL = 1e-6
 def initial_state(w):
     from paper_1506_04651_gb300 import inputs as I
     if w["gen"] == "cross":
-        return I.bz_cross_2d(w["J"], w["seed"])
+        return I.bz_cross_2d(w["J"], w["seed"], w=w.get("w", 0.02), amp=w.get("amp", 0.01))
     if w["gen"] == "front":
         return I.bz_front_2d(w["J"], w["seed"])
     return I.bz_sphere_3d(w["J"], w["seed"])
+
+
+def profiled_traffic(kernel_file, summary):
+    """DRAM bytes per launch recorded in profiles/<summary> by an ncu capture,
+    or None when the kernel's source has changed since that capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_1506_04651_gb300", "csrc", kernel_file), "rb").read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha256_16: ([0-9a-f]{16})", text)
+    tb = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    if not sha or not tb or hashlib.sha256(src).hexdigest()[:16] != sha.group(1):
+        return None
+    return int(tb.group(1))
 
 
 def measured_peaks():
@@ -230,19 +253,25 @@ def run_gpu(args, w):
     if rad_ms >= rock_ms:
         ach = rad_fl / (rad_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_radau (Radau5, FP64)", "achieved": ach, "peak": fp64_tf,
-                "unit": "TFLOP/s", "frac": ach / fp64_tf, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / fp64_tf,
+                "traffic": profiled_traffic("radau5.cu", "k_radau_bz2d_J10.md")
+                if args.workload == DEFAULT else None,
                 "peak_source": "measured FP64 FMA rate of this GPU (library probe, 2 flop/FMA)",
                 "launches": rad_n, "ms_per_launch": rad_ms / max(rad_n, 1)}
     else:
         ach = rock_b / (rock_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "k_rock (ROCK4 sweep, FP64)", "achieved": ach,
-                "peak": hbm or 6800.0, "unit": "GB/s", "frac": ach / (hbm or 6800.0), "traffic": None,
+                "peak": hbm or 6800.0, "unit": "GB/s", "frac": ach / (hbm or 6800.0),
+                "traffic": profiled_traffic("rock4.cu", "k_rock_persistent_bz2d_J10.md")
+                if args.workload == DEFAULT else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s",
                 "launches": rock_n, "ms_per_launch": rock_ms / max(rock_n, 1)}
     kernels = {"radau": {"ms": rad_ms, "launches": rad_n, "tflops": rad_fl / max(rad_ms, 1e-9) / 1e9},
                "rock": {"ms": rock_ms, "launches": rock_n,
                         "gbs": rock_b / max(rock_ms, 1e-9) / 1e6},
-               "step_ms": ms / args.steps}
+               "step_ms": ms / args.steps,
+               "last_step_phase_ms": {"adapt_and_tables": st1["ms_adapt"], "react_both_halves": st1["ms_react"],
+                                      "diffuse": st1["ms_diffuse"]}}
 
     # end to end through the C-ABI with host buffers: state in from pinned host
     # memory, one step, state out, every step
@@ -274,6 +303,13 @@ def run_gpu(args, w):
            "d2h_bytes_per_step": d2h // n_e2e, "steps": n_e2e,
            "note": "mr_set_leaves(host) + strang_step + mr_get_leaves(host) per step, wall clock"}
 
+    # mixed form (FP32 Newton factorisations in Radau5) on the same workload and
+    # the same number of steps from the same initial grid; its final state is
+    # compared with the FP64 path's after the same steps (relative L1 on the
+    # finest grid)
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed(args, w, mr, torch, dev, stream, u0)
     if pg:
         pg.barrier()
     if rank != 0:
@@ -294,12 +330,147 @@ def run_gpu(args, w):
                        "leaves_last_step": st["leaves"], "compression_ratio": st["compression_ratio"],
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk,
+            "gpu_launches": launches, "clocks": clk, "mixed": mixed,
             "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
     print(json.dumps(line), flush=True)
     ctx.close()
     if pg:
         pg.destroy_process_group()
+
+
+def finest_grid(keys, vals, d, J):
+    """Leaf values injected piecewise-constant onto the level-J grid."""
+    n = 1 << J
+    lev = (keys >> np.uint64(48)).astype(np.int64)
+    code = (keys & np.uint64((1 << 48) - 1)).astype(np.int64)
+    k = np.zeros((d, len(keys)), dtype=np.int64)
+    for b in range(J):
+        for a in range(d):
+            k[a] |= ((code >> (d * b + (d - 1 - a))) & 1) << b
+    out = np.zeros((vals.shape[0],) + (n,) * d)
+    for j in np.unique(lev):
+        sel = lev == j
+        bsz = 1 << (J - j)
+        for r in np.nonzero(sel)[0]:
+            sl = tuple(slice(k[a, r] * bsz, (k[a, r] + 1) * bsz) for a in reversed(range(d)))
+            out[(slice(None),) + sl] = vals[:, r][(slice(None),) + (None,) * d]
+    return out.reshape(vals.shape[0], -1)
+
+
+def run_mixed(args, w, mr, torch, dev, stream, u0):
+    nsteps = args.warmup + args.steps
+    res = {}
+    for prec in (mr.MR_FP64, mr.MR_MIXED):
+        c = mr.Context(mr.problem(w["d"], w["J"], precision=prec), stream=stream)
+        c.build(torch.from_numpy(u0).to(dev), w["eta"])
+        for _ in range(args.warmup):
+            c.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms, leaves = 0.0, 0
+        for _ in range(args.steps):
+            e0.record(stream)
+            c.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            leaves += c.stats()["leaves"]
+        keys, vals = c.leaves()
+        res[prec] = (leaves / (ms * 1e-3), ms / args.steps, keys, vals)
+        c.close()
+    f64 = finest_grid(res[mr.MR_FP64][2], res[mr.MR_FP64][3], w["d"], w["J"])
+    mix = finest_grid(res[mr.MR_MIXED][2], res[mr.MR_MIXED][3], w["d"], w["J"])
+    err = max(float(np.sum(np.abs(mix[i] - f64[i])) / np.sum(np.abs(f64[i]))) for i in range(len(f64)))
+    return {"value": res[mr.MR_MIXED][0], "ms_per_step": res[mr.MR_MIXED][1],
+            "fp64_value_same_run": res[mr.MR_FP64][0], "speedup_vs_fp64": res[mr.MR_MIXED][0] / res[mr.MR_FP64][0],
+            "rel_l1_vs_fp64_path": err, "steps": nsteps,
+            "form": "Radau5 Newton factorisations and solves in FP32; residuals, error estimates, "
+                    "step control, state, diffusion, details and mass in FP64",
+            "note": "no L2 flush between these steps; the FP64 path matches the oracle to 1e-9 per step"}
+
+
+def run_batch(args, b):
+    """Batched serving workload: every instance steps on its own stream; the GPU
+    overlaps their kernels.  value = leaves of all instances and steps / the
+    device makespan (start event on the default stream, which every instance
+    stream waits on, to the latest end event)."""
+    import concurrent.futures as cf
+
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1506_04651_gb300 import inputs as I
+    from paper_1506_04651_gb300 import mr
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    insts = I.batch_instances(b["n"])
+    streams = [torch.cuda.Stream(device=dev) for _ in insts]
+    ctxs = []
+    for inst, st in zip(insts, streams):
+        p = mr.problem(2, inst["J"], params=(1e-2, 1e-5, inst["f"], 2e-3))
+        c = mr.Context(p, stream=st)
+        u0 = I.bz_front_smooth_2d(inst["J"], inst["seed"] & 0xFFFFFFFF, x0=inst["x0"], f=inst["f"])
+        c.build(torch.from_numpy(u0).to(dev), inst["eta"])
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    pool = cf.ThreadPoolExecutor(max_workers=min(len(ctxs), 32))
+
+    def run(i, k):
+        n = 0
+        for _ in range(k):
+            ctxs[i].strang(b["dt"], insts[i]["eta"], TOL, TOL, TOL)
+            n += ctxs[i].stats()["leaves"]
+        return n
+
+    list(pool.map(lambda i: run(i, args.warmup), range(len(ctxs))))
+    torch.cuda.synchronize()
+    st0 = [c.stats() for c in ctxs]
+    start = torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event(enable_timing=True) for _ in ctxs]
+    clocks = ClockSampler(local)
+    clocks.start()
+    start.record(torch.cuda.current_stream())
+    for st in streams:
+        st.wait_event(start)
+
+    def timed(i):
+        n = run(i, args.steps)
+        ends[i].record(streams[i])
+        return n
+
+    leaves = sum(pool.map(timed, range(len(ctxs))))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max(start.elapsed_time(e) for e in ends)
+    st1 = [c.stats() for c in ctxs]
+    launches = sum(b1["kernel_launches"] - a["kernel_launches"] for a, b1 in zip(st0, st1))
+    rad_ms = sum(b1["radau_kernel_ms"] - a["radau_kernel_ms"] for a, b1 in zip(st0, st1))
+    rad_fl = sum(b1["radau_alg_flops"] - a["radau_alg_flops"] for a, b1 in zip(st0, st1))
+    fp64_tf, _ = mr.fp64_fma_rate()
+    # Radau5 kernels of different instances overlap, so the achieved FP64 rate
+    # of the batch is its algorithmic FP64 work over the makespan
+    ach = rad_fl / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_radau (Radau5, FP64), all instances", "achieved": ach,
+            "peak": fp64_tf, "unit": "TFLOP/s", "frac": ach / fp64_tf, "traffic": None,
+            "peak_source": "measured FP64 FMA rate of this GPU (library probe)",
+            "note": "algorithmic FP64 work of all Radau5 launches / batch makespan",
+            "radau_kernel_ms_summed_over_streams": rad_ms}
+    line = {"metric": METRIC, "value": leaves / (ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": b["desc"], "instances": len(ctxs),
+                       "J": [i["J"] for i in insts],
+                       "leaves_total_last_step": sum(s["leaves"] for s in st1),
+                       "l2": "inputs larger than L2 (all instances' state and work vectors)"},
+            "roofline": roof, "gpu_launches": launches, "clocks": clk}
+    pool.shutdown()
+    for c in ctxs:
+        c.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -308,11 +479,18 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCH))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.workload in BATCH:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-instance workloads"}))
+            return
+        run_batch(args, BATCH[args.workload])
+        return
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)

@@ -435,66 +435,78 @@ __global__ void k_irr_index(const int32_t* __restrict__ irr_flag, const int32_t*
   }
 }
 
-// Merged rows of the leaves at level jumps.  One warp builds one row:
-// the row's faces seed a shared-memory queue of (level, cell, weight) items;
-// every round each lane resolves one item through the direct map -- a leaf
-// adds its weight to the row (shared-memory hash keyed by leaf index), an
-// internal cell pushes its 2^d children with weight / 2^d (projection), an
-// absent cell pushes its parent's 3^d prediction stencil (Eq. inter_1d) --
-// until the queue is empty.  The merged row is sorted by leaf index (so the
-// sums the sweeps take are reproducible run to run) and written to a fixed
-// slot of the row.  Weights are dyadic, so merging is exact in any order.
+// Merged rows of the leaves at level jumps.  One warp builds one row.  The
+// row's faces name cells (level, position, weight): the same-level neighbour
+// and the row's own leaf, or, across a finer face, the touching children and
+// the row's own (absent) children.  Cells are merged in a shared-memory table
+// keyed by (level, Morton code) as they are named, and resolved level by
+// level so that every cell is expanded once with its summed weight:
+//   up:   absent cells from the finest level to the coarsest, each replaced by
+//         its parent's 3^d prediction stencil (Eq. inter_1d, mirror cells at
+//         the boundary);
+//   down: internal cells from the coarsest level to the finest, each replaced
+//         by its 2^d children with weight / 2^d (projection).
+// An absent cell only names cells one level coarser and an internal cell only
+// existing cells one level finer, so each cell's weight is complete when its
+// level is resolved.  What remains are leaves; the row is sorted by leaf index
+// (so the sweeps' sums are reproducible run to run) and written to a fixed
+// slot.  Weights are dyadic, so merging is exact in any order.
 template <int D>
 struct IrrCfg;
 template <>
 struct IrrCfg<2> {
-  static constexpr int kQueue = 256, kHash = 256, kWarps = 4;
+  static constexpr int kCells = 256, kSort = 128, kWarps = 4;
 };
 template <>
 struct IrrCfg<3> {
-  static constexpr int kQueue = 8192, kHash = 2048, kWarps = 1;
+  static constexpr int kCells = 1024, kSort = 1024, kWarps = 2;
 };
 
-struct QItem {
-  double w;
-  int16_t k[3];
-  int8_t j, pad;
-};
+constexpr unsigned long long kEmptyCell = ~0ull;
+constexpr int32_t kAbsent = -1, kInternal = -2;
 
 template <int D>
 struct IrrShared {
-  QItem q[IrrCfg<D>::kQueue];
-  int32_t key[IrrCfg<D>::kHash];
-  double val[IrrCfg<D>::kHash];
-  int head, tail, n, bad;
+  unsigned long long key[IrrCfg<D>::kCells];  // (level << 48) | Morton code
+  double w[IrrCfg<D>::kCells];
+  int32_t st[IrrCfg<D>::kCells];  // leaf index, kAbsent or kInternal
+  int16_t order[IrrCfg<D>::kCells];  // table slots in the order the cells were named
+  int32_t skey[IrrCfg<D>::kSort];
+  double sval[IrrCfg<D>::kSort];
+  int n, cnt, lo, hi, bad;
 };
 
-__device__ inline void hash_add(int32_t* key, double* val, int cap, int32_t c, double w, int* bad) {
-  uint32_t s = ((uint32_t)c * 2654435761u) & (cap - 1);
-  for (int probe = 0; probe < cap; probe++) {
-    int32_t old = atomicCAS(&key[s], -1, c);
-    if (old == -1 || old == c) {
-      atomicAdd(&val[s], w);
-      return;
-    }
-    s = (s + 1) & (cap - 1);
-  }
-  atomicExch(bad, 1);
-}
+struct IrrMaps {
+  const int32_t* dmap;
+  const int32_t* node_leaf;
+};
 
 template <int D>
-__device__ inline void qpush(IrrShared<D>& S, int j, const int* k, double w) {
-  int pos = atomicAdd(&S.tail, 1);
-  if (pos - S.head >= IrrCfg<D>::kQueue) {  // head only moves between rounds
-    atomicExch(&S.bad, 1);
-    return;
+__device__ inline void cell_add(IrrShared<D>& S, const IrrMaps& M, const Level& L, int j, const int* k,
+                                double w) {
+  constexpr int kC = IrrCfg<D>::kCells;
+  const uint32_t code = morton<D>(k);
+  const unsigned long long key = ((unsigned long long)j << 48) | code;
+  uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (kC - 1);
+  for (int probe = 0; probe < kC; probe++) {
+    const unsigned long long old = atomicCAS(&S.key[h], kEmptyCell, key);
+    if (old == kEmptyCell) {
+      const int32_t idx = M.dmap[L.doff[j] + code];
+      S.st[h] = idx < 0 ? kAbsent : (M.node_leaf[idx] >= 0 ? M.node_leaf[idx] : kInternal);
+      const int pos = atomicAdd(&S.n, 1);
+      S.order[pos] = (int16_t)h;
+      atomicMin(&S.lo, j);
+      atomicMax(&S.hi, j);
+      atomicAdd(&S.w[h], w);
+      return;
+    }
+    if (old == key) {
+      atomicAdd(&S.w[h], w);
+      return;
+    }
+    h = (h + 1) & (kC - 1);
   }
-  QItem& it = S.q[pos & (IrrCfg<D>::kQueue - 1)];
-  it.w = w;
-  it.j = (int8_t)j;
-  it.k[0] = (int16_t)k[0];
-  it.k[1] = (int16_t)k[1];
-  it.k[2] = (int16_t)(D == 3 ? k[2] : 0);
+  atomicExch(&S.bad, 1);
 }
 
 template <int D>
@@ -505,24 +517,28 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
                int32_t* __restrict__ cnt, int32_t* __restrict__ col, double* __restrict__ wout,
                unsigned long long* rho_bits, DevCounters* dc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kH = IrrCfg<D>::kHash, kQ = IrrCfg<D>::kQueue;
+  constexpr int kC = IrrCfg<D>::kCells, kS = IrrCfg<D>::kSort;
   IrrShared<D>& S = reinterpret_cast<IrrShared<D>*>(smem_raw)[threadIdx.x >> 5];
+  const IrrMaps M{dmap, node_leaf};
   const int lane = threadIdx.x & 31;
+  for (int q = lane; q < kC; q += 32) {
+    S.key[q] = kEmptyCell;
+    S.w[q] = 0.0;
+  }
+  if (lane == 0) S.n = 0;
+  __syncwarp();
   for (int64_t row = (int64_t)blockIdx.x * IrrCfg<D>::kWarps + (threadIdx.x >> 5); row < nrows;
        row += (int64_t)gridDim.x * IrrCfg<D>::kWarps) {
-    for (int q = lane; q < kH; q += 32) {
-      S.key[q] = -1;
-      S.val[q] = 0.0;
-    }
     if (lane == 0) {
-      S.head = S.tail = S.n = 0;
-      S.bad = 0;
+      S.cnt = S.bad = 0;
+      S.lo = 1 << 20;
+      S.hi = -1;
     }
     __syncwarp();
     const int32_t r = irr_leaf[row];
     const int32_t n = leaf_node[r];
     const int j = lvl[n];
-    int k[3];
+    int k[3] = {0, 0, 0};
     unmorton<D>(code[n], k);
     const int lim = 1 << j;
     const double ih2 = ldexp(1.0, 2 * j);
@@ -532,10 +548,10 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
       int q[3] = {k[0], k[1], k[2]};
       q[a] += sg;
       if (q[a] >= 0 && q[a] < lim) {  // homogeneous Neumann: no flux through the boundary
-        int32_t idx = dmap[L.doff[j] + morton<D>(q)];
+        const int32_t idx = dmap[L.doff[j] + morton<D>(q)];
         if (idx < 0 || node_leaf[idx] >= 0) {
-          qpush<D>(S, j, q, ih2);  // same-level leaf, or ghost by prediction
-          hash_add(S.key, S.val, kH, r, -ih2, &S.bad);
+          cell_add<D>(S, M, L, j, q, ih2);  // same-level leaf, or ghost by prediction
+          cell_add<D>(S, M, L, j, k, -ih2);
         } else {
           // finer side: minus the mean of the fluxes into the touching children
           for (int t = 0; t < (1 << D); t++) {
@@ -544,93 +560,97 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
             if (c[a] != 2 * q[a] + (sg > 0 ? 0 : 1)) continue;
             int g[3] = {c[0], c[1], c[2]};
             g[a] -= sg;
-            qpush<D>(S, j + 1, g, -coef);
-            qpush<D>(S, j + 1, c, coef);
+            cell_add<D>(S, M, L, j + 1, g, -coef);
+            cell_add<D>(S, M, L, j + 1, c, coef);
           }
         }
       }
     }
     __syncwarp();
-    for (int round = 0; round < 4096; round++) {
-      const int head = S.head, tail = S.tail;
-      if (head >= tail || S.bad) break;
-      const int mine = head + lane;
-      const bool have = mine < tail;
-      QItem it;
-      if (have) it = S.q[mine & (kQ - 1)];
+    // up: absent cells, finest level first
+    // (the pass's bounds are read by every lane before any lane adds a cell)
+    for (int jj = S.hi;; jj--) {
+      const bool go = jj >= 1 && jj >= S.lo && !S.bad;
+      const int ne = S.n;
       __syncwarp();
-      if (lane == 0) S.head = min(tail, head + 32);
-      __syncwarp();
-      if (have) {
+      if (!go) break;
+      for (int e = lane; e < ne; e += 32) {
+        const int h = S.order[e];
+        if ((int)(S.key[h] >> 48) != jj || S.st[h] != kAbsent) continue;
         int c[3] = {0, 0, 0};
-        const int jj = it.j;
-        for (int a = 0; a < D; a++) c[a] = mirror(it.k[a], jj);
-        int32_t idx = dmap[L.doff[jj] + morton<D>(c)];
-        if (idx >= 0) {
-          int32_t li = node_leaf[idx];
-          if (li >= 0) {
-            hash_add(S.key, S.val, kH, li, it.w, &S.bad);
-          } else {
-            const double w = it.w * (1.0 / (1 << D));
-            for (int t = 0; t < (1 << D); t++) {
-              int ch[3] = {0, 0, 0};
-              for (int a = 0; a < D; a++) ch[a] = 2 * c[a] + ((t >> a) & 1);
-              qpush<D>(S, jj + 1, ch, w);
-            }
+        unmorton<D>((uint32_t)(S.key[h] & 0xffffffffffffull), c);
+        const double wc = S.w[h];
+        constexpr int NST = D == 2 ? 9 : 27;
+        for (int o = 0; o < NST; o++) {
+          int oo = o, s[3] = {0, 0, 0};
+          double w = wc;
+          for (int a = 0; a < D; a++) {
+            const int off = oo % 3 - 1;
+            oo /= 3;
+            s[a] = mirror((c[a] >> 1) + off, jj - 1);
+            w *= wpred(c[a] & 1, off);
           }
-        } else {
-          constexpr int NST = D == 2 ? 9 : 27;
-          for (int o = 0; o < NST; o++) {
-            int oo = o, st[3] = {0, 0, 0};
-            double w = it.w;
-            for (int a = 0; a < D; a++) {
-              int off = oo % 3 - 1;
-              oo /= 3;
-              st[a] = (c[a] >> 1) + off;
-              w *= wpred(c[a] & 1, off);
-            }
-            qpush<D>(S, jj - 1, st, w);
-          }
+          cell_add<D>(S, M, L, jj - 1, s, w);
         }
       }
       __syncwarp();
     }
-    __syncwarp();
-    if (S.head < S.tail) S.bad = 1;  // round limit reached
-    // compact the non-zero entries, then sort them by leaf index
-    int32_t* skey = reinterpret_cast<int32_t*>(S.q);  // the queue is free now
-    double* sval = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(S.q) + sizeof(int32_t) * kH);
-    static_assert(sizeof(QItem) * kQ >= (sizeof(int32_t) + sizeof(double)) * kH, "queue too small to sort in");
-    __syncwarp();
-    for (int q = lane; q < kH; q += 32) {
-      if (S.key[q] >= 0 && S.val[q] != 0.0) {
-        int pos = atomicAdd(&S.n, 1);
-        skey[pos] = S.key[q];
-        sval[pos] = S.val[q];
+    // down: internal cells, coarsest level first
+    for (int jj = S.lo;; jj++) {
+      const bool go = jj <= S.hi && !S.bad;
+      const int ne = S.n;
+      __syncwarp();
+      if (!go) break;
+      for (int e = lane; e < ne; e += 32) {
+        const int h = S.order[e];
+        if ((int)(S.key[h] >> 48) != jj || S.st[h] != kInternal) continue;
+        int c[3] = {0, 0, 0};
+        unmorton<D>((uint32_t)(S.key[h] & 0xffffffffffffull), c);
+        const double w = S.w[h] * (1.0 / (1 << D));
+        for (int t = 0; t < (1 << D); t++) {
+          int ch[3] = {0, 0, 0};
+          for (int a = 0; a < D; a++) ch[a] = 2 * c[a] + ((t >> a) & 1);
+          cell_add<D>(S, M, L, jj + 1, ch, w);
+        }
+      }
+      __syncwarp();
+    }
+    // collect the leaves with non-zero weight, then sort them by leaf index
+    const int ne = S.n;
+    for (int e = lane; e < ne; e += 32) {
+      const int h = S.order[e];
+      if (S.st[h] >= 0 && S.w[h] != 0.0) {
+        const int pos = atomicAdd(&S.cnt, 1);
+        if (pos < kS) {
+          S.skey[pos] = S.st[h];
+          S.sval[pos] = S.w[h];
+        } else {
+          atomicExch(&S.bad, 1);
+        }
       }
     }
     __syncwarp();
-    const int cntr = S.n;
+    const int cntr = min(S.cnt, kS);
     int np2 = 1;
     while (np2 < cntr) np2 <<= 1;
     for (int q = cntr + lane; q < np2; q += 32) {
-      skey[q] = 0x7fffffff;
-      sval[q] = 0.0;
+      S.skey[q] = 0x7fffffff;
+      S.sval[q] = 0.0;
     }
     __syncwarp();
     for (int size = 2; size <= np2; size <<= 1)
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
         for (int q = lane; q < np2; q += 32) {
-          int p = q ^ stride;
+          const int p = q ^ stride;
           if (p > q) {
-            bool up = (q & size) == 0;
-            if ((skey[q] > skey[p]) == up) {
-              int32_t tk = skey[q];
-              skey[q] = skey[p];
-              skey[p] = tk;
-              double tv = sval[q];
-              sval[q] = sval[p];
-              sval[p] = tv;
+            const bool up = (q & size) == 0;
+            if ((S.skey[q] > S.skey[p]) == up) {
+              const int32_t tk = S.skey[q];
+              S.skey[q] = S.skey[p];
+              S.skey[p] = tk;
+              const double tv = S.sval[q];
+              S.sval[q] = S.sval[p];
+              S.sval[p] = tv;
             }
           }
         }
@@ -639,18 +659,25 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
     double sa = 0.0;
     const bool ok = !S.bad && cntr <= slot;
     for (int q = lane; q < cntr; q += 32) {
-      sa += fabs(sval[q]);
+      sa += fabs(S.sval[q]);
       if (ok) {
-        col[row * (int64_t)slot + q] = skey[q];
-        wout[row * (int64_t)slot + q] = sval[q];
+        col[row * (int64_t)slot + q] = S.skey[q];
+        wout[row * (int64_t)slot + q] = S.sval[q];
       }
     }
     for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    // empty the table for the next row (only the slots this row used)
+    for (int e = lane; e < ne; e += 32) {
+      const int h = S.order[e];
+      S.key[h] = kEmptyCell;
+      S.w[h] = 0.0;
+    }
     if (lane == 0) {
       cnt[row] = ok ? cntr : 0;
       if (!ok) atomicExch(&dc->overflow, 1);
       atomicAdd(reinterpret_cast<unsigned long long*>(&dc->irr_nnz), (unsigned long long)cntr);
       atomicMax(rho_bits, (unsigned long long)__double_as_longlong(sa));
+      S.n = 0;
     }
     __syncwarp();
   }

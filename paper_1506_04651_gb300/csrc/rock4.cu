@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "mr_internal.cuh"
@@ -614,15 +615,22 @@ int build_coeffs(int s, Coeffs& C) {
   return 0;
 }
 
+// every stage count's coefficients, built once per process (thread-safe:
+// contexts on several host threads share them)
 std::vector<Coeffs>& coeff_cache() {
-  static std::vector<Coeffs> cache(kSmax + 1);
+  static std::vector<Coeffs> cache = [] {
+    std::vector<Coeffs> v(kSmax + 1);
+    for (int s = kSmin; s <= kSmax; s++)
+      if (build_coeffs(s, v[s])) v[s].s = 0;
+    return v;
+  }();
   return cache;
 }
 
 const Coeffs* get_coeffs(int s) {
-  Coeffs& C = coeff_cache()[s];
-  if (C.s != s && build_coeffs(s, C)) return nullptr;
-  return &C;
+  if (s < kSmin || s > kSmax) return nullptr;
+  const Coeffs& C = coeff_cache()[s];
+  return C.s == s ? &C : nullptr;
 }
 
 }  // namespace
@@ -661,6 +669,22 @@ static double sweep_bytes(const mr_ctx* c, const StageArgs& A, int64_t N) {
   return N * (per_leaf + 8.0 * c->d + 1.0) + 12.0 * c->stats.irregular_nnz + 8.0 * c->stats.irregular_rows;
 }
 
+// 1/h_j^2 of every level in constant memory, written once per device
+static std::mutex g_ih2_mu;
+static bool g_ih2_done[256] = {false};
+
+static mr_status init_ih2(mr_ctx* c) {
+  int dev = 0;
+  MR_CUDA(c, cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_ih2_mu);
+  if (dev >= 0 && dev < 256 && g_ih2_done[dev]) return MR_OK;
+  double ih2[kMaxL + 1];
+  for (int j = 0; j <= kMaxL; j++) ih2[j] = ldexp(1.0, 2 * j);
+  MR_CUDA(c, cudaMemcpyToSymbol(c_ih2, ih2, sizeof ih2));
+  if (dev >= 0 && dev < 256) g_ih2_done[dev] = true;
+  return MR_OK;
+}
+
 static void launch_rock(mr_ctx* c, const StageArgs& A, int64_t N, int nb, int* nev = nullptr) {
   if (nev && *nev < 256) cudaEventRecord(c->tev[2 * *nev], c->stream);
   IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_slot};
@@ -680,9 +704,7 @@ static void launch_rock(mr_ctx* c, const StageArgs& A, int64_t N, int nb, int* n
 mr_status apply_operator(mr_ctx* c, const double* in, double* out) {
   mr_status st = build_tables(c);
   if (st) return st;
-  double ih2[kMaxL + 1];
-  for (int j = 0; j <= kMaxL; j++) ih2[j] = ldexp(1.0, 2 * j);
-  MR_CUDA(c, cudaMemcpyToSymbolAsync(c_ih2, ih2, sizeof ih2, 0, cudaMemcpyHostToDevice, c->stream));
+  MR_TRY(init_ih2(c));
   StageArgs A;
   memset(&A, 0, sizeof A);
   A.nspec = 1;
@@ -701,23 +723,40 @@ mr_status apply_operator(mr_ctx* c, const double* in, double* out) {
 }
 
 // device coefficient table for every s (built once per process on the host)
-static const double* device_table(mr_ctx* c, RockTab* tab) {
-  static std::vector<double> host;
-  static int off[kSmax + 1];
-  if (host.empty()) {
+struct HostTable {
+  std::vector<double> data;
+  int off[kSmax + 1] = {0};
+  bool ok = true;
+};
+
+static const HostTable& host_table() {
+  static const HostTable T = [] {
+    HostTable t;
     for (int s = kSmin; s <= kSmax; s++) {
       const Coeffs* C = get_coeffs(s);
-      if (!C) return nullptr;
-      off[s] = (int)host.size();
+      if (!C) {
+        t.ok = false;
+        break;
+      }
+      t.off[s] = (int)t.data.size();
       const int n = s - 4;
-      host.push_back(C->ell);
-      for (int k = 0; k < 5; k++) host.push_back(C->w[k]);
-      for (int k = 0; k < 4; k++) host.push_back(C->errc[k]);
-      for (int j = 1; j <= n; j++) host.push_back(C->mu[j]);
-      for (int j = 1; j <= n; j++) host.push_back(C->nu[j]);
-      for (int j = 1; j <= n; j++) host.push_back(C->kap[j]);
+      t.data.push_back(C->ell);
+      for (int k = 0; k < 5; k++) t.data.push_back(C->w[k]);
+      for (int k = 0; k < 4; k++) t.data.push_back(C->errc[k]);
+      for (int j = 1; j <= n; j++) t.data.push_back(C->mu[j]);
+      for (int j = 1; j <= n; j++) t.data.push_back(C->nu[j]);
+      for (int j = 1; j <= n; j++) t.data.push_back(C->kap[j]);
     }
-  }
+    return t;
+  }();
+  return T;
+}
+
+static const double* device_table(mr_ctx* c, RockTab* tab) {
+  const HostTable& T = host_table();
+  if (!T.ok) return nullptr;
+  const std::vector<double>& host = T.data;
+  const int* off = T.off;
   if (!c->rock_tab) {
     if (cudaMalloc(&c->rock_tab, sizeof(double) * host.size()) != cudaSuccess) return nullptr;
     if (cudaMemcpy(c->rock_tab, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -733,9 +772,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   if (st) return st;
   const int m = c->m;
   const int64_t N = c->tb[c->cur].nleaves;
-  double ih2[kMaxL + 1];
-  for (int j = 0; j <= kMaxL; j++) ih2[j] = ldexp(1.0, 2 * j);
-  MR_CUDA(c, cudaMemcpyToSymbolAsync(c_ih2, ih2, sizeof ih2, 0, cudaMemcpyHostToDevice, c->stream));
+  MR_TRY(init_ih2(c));
   PersArgs P;
   memset(&P, 0, sizeof P);
   if (!device_table(c, &P.tab)) {

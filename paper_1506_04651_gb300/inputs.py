@@ -86,16 +86,27 @@ def bz_front_2d(J: int, seed: int, x0: float = 0.5, w: float = 0.02, noise: floa
 
 
 def bz_cross_2d(J: int, seed: int, w: float = 0.02, f: float = BZ_DEFAULT["f"],
-                q: float = BZ_DEFAULT["q"], be: float = 0.8, x0: float = 0.5, y0: float = 0.5):
+                q: float = BZ_DEFAULT["q"], be: float = 0.8, x0: float = 0.5, y0: float = 0.5,
+                amp: float = 0.01):
     """Two crossing fronts: b from a front along x = x0(y), c from a front along y = y0(x),
-    both positions perturbed by smooth seeded Fourier noise."""
+    both positions perturbed by smooth seeded Fourier noise of amplitude amp."""
     x, y = cell_centres(2, J)
     br = bz_rest_state(f, q)
-    px = x0 + _fourier(seed, y)
-    py = y0 + _fourier(seed + 1, x)
+    px = x0 + _fourier(seed, y, amp=amp)
+    py = y0 + _fourier(seed + 1, x, amp=amp)
     b = br + (be - br) * _profile(x - px, w)
     c = br + (be - br) * _profile(y - py, w)
     return bz_state(b, c, f, q)
+
+
+def bz_front_smooth_2d(J: int, seed: int, x0: float = 0.5, f: float = BZ_DEFAULT["f"],
+                       q: float = BZ_DEFAULT["q"], w: float = 0.02, amp: float = 0.02, be: float = 0.8):
+    """One front along x = x0(y) (smooth seeded position noise), rest state of the
+    instance's f: the per-instance initial state of the batched workload."""
+    x, y = cell_centres(2, J)
+    br = bz_rest_state(f, q)
+    b = br + (be - br) * _profile(x - (x0 + _fourier(seed, y, amp=amp)), w)
+    return bz_state(b, b.copy(), f, q)
 
 
 def bz_sphere_3d(J: int, seed: int, r0: float = 0.3, w: float = 0.02,

@@ -1,12 +1,12 @@
 """GPU parity: every step of the hot path, run through the C-ABI on the GPU,
 against the oracle on identical seeded inputs.
 
-Tolerances (the design doc derives them): adaptation decisions are taken on both
+Tolerances: adaptation decisions are taken on both
 sides with the same FP64 detail arithmetic (same sum order, no fused
 multiply-add), so leaf sets and values after an adaptation must be identical;
 operator rows use dyadic weights, so the Gershgorin bound is exact and L u
 agrees to 1e-12 relative; one Radau5 / ROCK4 / Strang step agrees to 1e-9
-relative L-infinity per species (the bound the benchmark spec fixes); ten steps agree
+relative L-infinity per species (the FP64 one-step bound); ten steps agree
 to 1e-6 relative L1.
 """
 import numpy as np
