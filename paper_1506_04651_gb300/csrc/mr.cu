@@ -435,6 +435,26 @@ __global__ void k_irr_index(const int32_t* __restrict__ irr_flag, const int32_t*
   }
 }
 
+// Compact table of the regular leaves (every face meets a same-level leaf or
+// the boundary), in leaf order: leaf index, the 2d neighbour indices and the
+// level in two 16-byte words, so that a sweep thread loads everything it
+// needs with two vector loads and no thread of a sweep idles on a leaf at a
+// level jump.
+__global__ void k_reg_table(const int32_t* __restrict__ irr_flag, const int32_t* __restrict__ irank,
+                            const int32_t* __restrict__ nbr, const uint8_t* __restrict__ leaf_lvl, int64_t N,
+                            int64_t capL, int D, int4* __restrict__ reg) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if (irr_flag[r]) continue;
+    const int64_t k = r - irank[r];
+    int v[8] = {(int)r, 0, 0, 0, 0, 0, 0, 0};
+    for (int f = 0; f < 2 * D; f++) v[1 + f] = nbr[f * capL + r];
+    v[1 + 2 * D] = leaf_lvl[r];
+    reg[2 * k] = make_int4(v[0], v[1], v[2], v[3]);
+    reg[2 * k + 1] = make_int4(v[4], v[5], v[6], v[7]);
+  }
+}
+
 // Merged rows of the leaves at level jumps.  One warp builds one row.  The
 // row's faces name cells (level, position, weight): the same-level neighbour
 // and the row's own leaf, or, across a finer face, the touching children and
@@ -936,8 +956,10 @@ mr_status build_tables(mr_ctx* c) {
                                                          c->cap_leaves, c->nbr, c->leaf_lvl, irr_flag, c->rho_bits);
   int32_t* irank = c->itmp + c->cap_leaves;
   scan_i32(c, irr_flag, irank, N, &c->dc->irr_rows);
+  k_reg_table<<<grid_for(N), kBlock, 0, c->stream>>>(irr_flag, irank, c->nbr, c->leaf_lvl, N, c->cap_leaves, D,
+                                                     c->reg_tab);
   k_irr_index<<<grid_for(N), kBlock, 0, c->stream>>>(irr_flag, irank, N, c->cap_leaves, c->nbr, c->irr_leaf);
-  c->launches += 2;
+  c->launches += 3;
   MR_TRY(sync_counts(c));
   const int64_t nrows = c->hc.irr_rows;
   const int slot = D == 2 ? kIrrSlot2 : kIrrSlot3;

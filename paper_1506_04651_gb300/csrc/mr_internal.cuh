@@ -135,6 +135,7 @@ struct mr_ctx {
   int32_t* nbr = nullptr;            // [2d][cap_leaves]
   uint8_t* leaf_lvl = nullptr;
   int32_t* irr_leaf = nullptr;       // [cap_leaves]
+  int4* reg_tab = nullptr;           // [2 cap_leaves]: per regular leaf (r, 2d neighbours, level)
   int32_t* irr_cnt = nullptr;        // [cap_leaves + 1]
   int64_t* irr_ptr = nullptr;        // [cap_leaves + 1]
   int32_t* irr_col = nullptr;
@@ -147,7 +148,7 @@ struct mr_ctx {
   unsigned long long* rho_bits = nullptr;
   bool tables_valid = false;
   // ROCK4 / reductions
-  double* work[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* work[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* red = nullptr;             // reduction partials
   double* red_out = nullptr;
   int32_t* complexity = nullptr;

@@ -137,9 +137,15 @@ __global__ void __launch_bounds__(kBlock) k_rock(StageArgs A, int64_t N, int64_t
 // species: ROCK4 steps are taken, accepted or rejected and resized on the
 // device, with grid-wide barriers between sweeps (the vectors of the
 // benchmark's grids are L2-resident, so a barrier is far cheaper than a kernel
-// launch and a host round trip per step).  Block 0, thread 0 runs the control
-// of every species with the host driver's arithmetic; everything else is the
-// same per-leaf sweep as k_rock.
+// launch and a host round trip per step).
+//
+// Every block keeps its own copy of the step control in shared memory and
+// runs the same control arithmetic on the same per-block error partials in
+// the same order, so all copies agree and no barrier is spent on a control
+// section.  An accepted step swaps the state with the buffer holding the
+// candidate (no copy sweep), and the operator applied to the candidate by the
+// embedded-estimate sweep is kept: it is L y_n of the next step, so the first
+// recurrence stage of every step but the first is a plain axpy.
 
 // coefficient table for s = 5..152: [l_s, w0..w4, e0..e3, mu_1..n, nu_1..n, kap_1..n]
 struct RockTab {
@@ -161,16 +167,17 @@ struct PersArgs {
   int64_t N, capL;
   double dt, tol, rho;
   double Dc[kMaxM];
-  double* U;
-  double* W[4];
-  double* part;  // [kMaxM][nb]
-  RockCtl* ctl;
+  double* U;     // the state; buffer 0 of each species' pool of four
+  double* W[6];  // W0..W2: pool buffers 1..3; W3: error accumulator; W4, W5: L y
+  double* part;  // [kMaxM][nb] per-block partial sums of the error norm
+  RockCtl* ctl;  // initial control in, final control out
   RockTab tab;
 };
 
 __device__ inline double ell_dev(int s) { return 0.336 * (double)s * s - 2.7; }
 
-// control section (one thread): choose the next step of every species
+// choose the next step of every species (one thread per block, on the
+// block's copy of the control)
 __device__ void rock_prepare(const PersArgs& P, RockCtl& C, int64_t N, double leafb) {
   int nmax = 0, any = 0;
   double bytes = 0.0;
@@ -205,30 +212,36 @@ __device__ void rock_prepare(const PersArgs& P, RockCtl& C, int64_t N, double le
     C.stages += s;
     C.smax = max(C.smax, s);
     C.matvecs += s + 1;
-    // sweep bytes: stages 16/24, Horner 16+24+32+40, FSAL 24
-    bytes += N * (16.0 + 24.0 * (s - 5) + 112.0 + 24.0);
+    // vector bytes per leaf: stage 1 24, stages 2..n 24, Horner 16+24+32+40,
+    // embedded estimate 24 + 8 (keeps L y_{n+1})
+    bytes += N * (24.0 * (s - 4) + 112.0 + 32.0);
     any = 1;
   }
   C.nmax = nmax;
-  C.bytes += bytes + (double)(nmax + 5) * leafb;
+  // neighbour tables: one gather sweep per stage 2..n and per finishing sweep
+  C.bytes += bytes + (double)(nmax - 1 + 5) * leafb;
   if (!any) C.finished = 1;
 }
 
-// operands of one species in one sweep of the persistent driver
-enum { K_STAGE = 0, K_H3, K_H2, K_H1, K_H0, K_FSAL };
-constexpr int kPhaseFinish = 1000;  // phases 1..n: stages; kPhaseFinish + K_*: finishing sweeps
+// operands of one species in one sweep
+enum { K_STAGE = 0, K_H3, K_H2, K_H1, K_H0, K_FSAL, K_STAGE1 };
+constexpr int kPhaseFinish = 1000;  // phases 2..n: stages; kPhaseFinish + K_*: the other sweeps
 
 struct Ops {
-  const double *x, *a, *b;
-  double *out, *acc;
+  const double *x, *a, *b, *yn;
+  double *out, *acc, *lx;
   double ca, cb, cl, e0, e1, e2;
   int kind;
 };
 
-__device__ inline void combine(const Ops& o, int64_t r, double Lx, const double* yn, double tol, double& err) {
+__device__ inline void combine(const Ops& o, int64_t r, double Lx, double tol, double& err) {
   switch (o.kind) {
     case K_STAGE:
-      o.out[r] = o.ca * o.a[r] + (o.b ? o.cb * o.b[r] : 0.0) + o.cl * Lx;
+      o.out[r] = o.ca * o.a[r] + o.cb * o.b[r] + o.cl * Lx;
+      break;
+    case K_STAGE1:  // first step only: P_1 = y + kap_1 h L y, keeping L y
+      o.lx[r] = Lx;
+      o.out[r] = o.ca * o.a[r] + o.cl * Lx;
       break;
     case K_H3:
     case K_H2:
@@ -246,122 +259,123 @@ __device__ inline void combine(const Ops& o, int64_t r, double Lx, const double*
       o.acc[r] += v;
       break;
     }
-    default: {  // embedded estimate e = acc + d z y_{n+1}
+    default: {  // embedded estimate e = acc + d z y_{n+1}; L y_{n+1} is kept
+      o.lx[r] = Lx;
       const double ee = o.acc[r] + o.cl * Lx;
-      const double sc = tol + tol * fmax(fabs(yn[r]), fabs(o.x[r]));
+      const double sc = tol + tol * fmax(fabs(o.yn[r]), fabs(o.x[r]));
       err += (ee / sc) * (ee / sc);
     }
   }
 }
 
 template <int D, int M>
-__global__ void __launch_bounds__(kBlock) k_rock_persistent(PersArgs P, const int32_t* __restrict__ nbr,
-                                                            const uint8_t* __restrict__ lvl, IrrRows R,
-                                                            const int32_t* __restrict__ irr_leaf, int64_t nirr) {
+__global__ void __launch_bounds__(kBlock, 2) k_rock_persistent(PersArgs P, const int4* __restrict__ reg, int64_t nreg,
+                                                            IrrRows R, const int32_t* __restrict__ irr_leaf,
+                                                            int64_t nirr) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[kBlock];
-  // per-block copy of the control fields the sweeps read, refreshed after each
-  // control section with loads that bypass L1
-  __shared__ int s_done[kMaxM], s_n[kMaxM], s_s[kMaxM], s_a[kMaxM], s_acc[kMaxM], s_cp[kMaxM];
-  __shared__ double s_h[kMaxM];
-  __shared__ int s_nmax, s_fin;
-  RockCtl& C = *P.ctl;
+  __shared__ RockCtl C;         // this block's copy of the step control
+  __shared__ int s_py[kMaxM];   // pool index of the state
+  __shared__ int s_pr[kMaxM][3];  // pool indices of the three recurrence buffers
+  __shared__ int s_ly[kMaxM];   // which of W4 / W5 holds L y of the state
+  __shared__ double s_err2[kMaxM];
+  __shared__ Ops s_ops[M];
+  __shared__ int s_act[M];
   const int64_t N = P.N, capL = P.capL;
-  auto refresh = [&]() {
-    if (threadIdx.x < M) {
-      const int i = threadIdx.x;
-      s_done[i] = __ldcg(&C.done[i]);
-      s_n[i] = __ldcg(&C.n[i]);
-      s_s[i] = __ldcg(&C.s[i]);
-      s_a[i] = __ldcg(&C.a[i]);
-      s_acc[i] = __ldcg(&C.acc_prev[i]);
-      s_cp[i] = __ldcg(&C.c_prev[i]);
-      s_h[i] = __ldcg(&C.h[i]);
+  if (threadIdx.x == 0) {
+    C = *P.ctl;
+    for (int i = 0; i < M; i++) {
+      s_py[i] = 0;
+      s_pr[i][0] = 1;
+      s_pr[i][1] = 2;
+      s_pr[i][2] = 3;
+      s_ly[i] = 0;
     }
-    if (threadIdx.x == 0) {
-      s_nmax = __ldcg(&C.nmax);
-      s_fin = __ldcg(&C.finished);
-    }
-    __syncthreads();
-  };
+  }
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   const double leafb = N * (8.0 * D + 1.0);
+  auto pool = [&](int i, int k) { return (k == 0 ? P.U : P.W[k - 1]) + (int64_t)i * capL; };
   auto Wp = [&](int q, int i) { return P.W[q] + (int64_t)i * capL; };
-  auto Up = [&](int i) { return P.U + (int64_t)i * capL; };
-  // operands of species i in `phase`, built once per sweep; false if the
-  // species sits this sweep out
+  auto Y = [&](int i) { return pool(i, s_py[i]); };
+  auto Rb = [&](int i, int q) { return pool(i, s_pr[i][q]); };
+  auto LY = [&](int i) { return Wp(4 + s_ly[i], i); };
+  auto LC = [&](int i) { return Wp(5 - s_ly[i], i); };
+  // operands of species i in `phase`; false if the species sits it out
   auto ops_for = [&](int phase, int i, Ops& o) -> bool {
-    if (s_done[i]) return false;
-    const double* tb = P.tab.data + P.tab.off[s_s[i]];
-    const double hd = s_h[i] * P.Dc[i];
+    if (C.done[i]) return false;
+    const double* tb = P.tab.data + P.tab.off[C.s[i]];
+    const double hd = C.h[i] * P.Dc[i];
+    const int n = C.n[i];
     o.b = nullptr;
     o.acc = nullptr;
-    if (phase < kPhaseFinish) {
-      const int j = phase, n = s_n[i];
+    o.lx = nullptr;
+    o.yn = Y(i);
+    if (phase < kPhaseFinish) {  // stage j >= 2
+      const int j = phase;
       if (j > n) return false;
       o.kind = K_STAGE;
-      o.x = j == 1 ? Up(i) : Wp((j - 2) % 3, i);
+      o.x = Rb(i, (j - 2) % 3);
       o.a = o.x;
-      o.b = j == 1 ? nullptr : (j == 2 ? Up(i) : Wp((j - 3) % 3, i));
-      o.out = Wp((j - 1) % 3, i);
+      o.b = j == 2 ? Y(i) : Rb(i, (j - 3) % 3);
+      o.out = Rb(i, (j - 1) % 3);
       o.ca = tb[10 + (j - 1)];
       o.cb = tb[10 + n + (j - 1)];
-      o.cl = tb[10 + 2 * n + (j - 1)] * s_h[i] * P.Dc[i];
+      o.cl = tb[10 + 2 * n + (j - 1)] * hd;
       return true;
     }
     const double* w = tb + 1;
     const double* e = tb + 6;
-    const int a = s_a[i], b = (a + 1) % 3, cc = (a + 2) % 3;
+    const int a = C.a[i], b = (a + 1) % 3, cc = (a + 2) % 3;
     o.kind = phase - kPhaseFinish;
     switch (o.kind) {
-      case K_H3: o.x = Wp(a, i); o.a = Wp(a, i); o.out = Wp(b, i); o.ca = w[3]; o.cl = w[4] * hd; break;
-      case K_H2: o.x = Wp(b, i); o.a = Wp(a, i); o.out = Wp(cc, i); o.ca = w[2]; o.cl = hd; break;
+      case K_STAGE1:
+        o.x = Y(i); o.a = Y(i); o.out = Rb(i, 0); o.lx = LY(i);
+        o.ca = tb[10]; o.cl = tb[10 + 2 * n] * hd;
+        break;
+      case K_H3: o.x = Rb(i, a); o.a = Rb(i, a); o.out = Rb(i, b); o.ca = w[3]; o.cl = w[4] * hd; break;
+      case K_H2: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.ca = w[2]; o.cl = hd; break;
       case K_H1:
-        o.x = Wp(cc, i); o.a = Wp(a, i); o.out = Wp(b, i); o.acc = Wp(3, i); o.ca = w[1]; o.cl = hd;
+        o.x = Rb(i, cc); o.a = Rb(i, a); o.out = Rb(i, b); o.acc = Wp(3, i); o.ca = w[1]; o.cl = hd;
         o.e0 = e[0]; o.e1 = e[1]; o.e2 = e[2];
         break;
-      case K_H0: o.x = Wp(b, i); o.a = Wp(a, i); o.out = Wp(cc, i); o.acc = Wp(3, i); o.ca = 1.0; o.cl = hd; break;
-      default: o.x = Wp(cc, i); o.a = nullptr; o.out = nullptr; o.acc = Wp(3, i); o.cl = e[3] * hd;
+      case K_H0: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.acc = Wp(3, i); o.ca = 1.0; o.cl = hd; break;
+      default:
+        o.x = Rb(i, cc); o.a = nullptr; o.out = nullptr; o.acc = Wp(3, i); o.lx = LC(i); o.cl = e[3] * hd;
     }
     return true;
   };
-  // one sweep: regular leaves one thread each (neighbour indices loaded once
-  // for all species), merged rows one warp each
-  __shared__ Ops s_ops[M];
-  __shared__ int s_act[M];
-  auto sweep = [&](int phase, double* err) {
-    // operands of every species, built once per sweep per block; read from
-    // shared memory so that they do not hold registers across the loops
+  auto build_ops = [&](int phase) {
     __syncthreads();
     if (threadIdx.x < M) s_act[threadIdx.x] = ops_for(phase, threadIdx.x, s_ops[threadIdx.x]);
     __syncthreads();
+  };
+  // one operator sweep: regular leaves one thread each from the compact
+  // table (neighbour indices loaded once for all species), merged rows four
+  // lanes each
+  constexpr int G = 4;
+  static_assert(M <= G, "one merged-row lane per species");
+  const int sub = lane & (G - 1);
+  auto sweep = [&](double* err, double& err_row) {
     const Ops* o = s_ops;
     const int* act = s_act;
-    for (int64_t r = tid; r < N; r += nth) {
-      const int32_t n0 = nbr[r];
-      if (n0 < 0) continue;
-      int32_t nb[2 * D];
-      nb[0] = n0;
-#pragma unroll
-      for (int f = 1; f < 2 * D; f++) nb[f] = nbr[f * capL + r];
-      const double ih2 = c_ih2[lvl[r]];
+    for (int64_t q = tid; q < nreg; q += nth) {
+      const int4 e0 = reg[2 * q], e1 = reg[2 * q + 1];
+      const int v[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+      const int64_t r = v[0];
+      const double ih2 = c_ih2[v[1 + 2 * D]];
 #pragma unroll
       for (int i = 0; i < M; i++) {
         if (!act[i]) continue;
         const double* x = o[i].x;
-        double sx = x[nb[0]];
+        double sx = x[v[1]];
 #pragma unroll
-        for (int f = 1; f < 2 * D; f++) sx += x[nb[f]];
-        combine(o[i], r, (sx - 2.0 * D * x[r]) * ih2, Up(i), P.tol, err[i]);
+        for (int f = 1; f < 2 * D; f++) sx += x[v[1 + f]];
+        combine(o[i], r, (sx - 2.0 * D * x[r]) * ih2, P.tol, err[i]);
       }
     }
-    // merged rows: 8 lanes per row, four rows per warp in flight; each entry's
-    // loads are issued for every species at once
-    constexpr int G = 8;
-    const int sub = lane & (G - 1);
-    const int64_t grp = (tid >> 3), ngrp = nth >> 3;
+    const int64_t grp = tid / G, ngrp = nth / G;
     const int64_t rounds = (nirr + ngrp - 1) / ngrp;
     for (int64_t k = 0; k < rounds; k++) {
       const int64_t row = grp + k * ngrp;
@@ -387,38 +401,62 @@ __global__ void __launch_bounds__(kBlock) k_rock_persistent(PersArgs P, const in
 #pragma unroll
       for (int i = 0; i < M; i++)
         for (int sft = G / 2; sft > 0; sft >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], sft);
-      if (have && sub == 0) {
+      // every lane of the group holds the row's sums; lane `sub` finishes
+      // species sub, sub + G, ... (one instruction stream for the species)
+      if (have) {
 #pragma unroll
-        for (int i = 0; i < M; i++)
-          if (act[i]) combine(o[i], r, v[i], Up(i), P.tol, err[i]);
+        for (int i0 = 0; i0 < M; i0 += G) {
+          const int i = i0 + sub;
+          double vi = v[i0];
+#pragma unroll
+          for (int u = 1; u < G; u++)
+            if (i0 + u < M && sub == u) vi = v[i0 + u];
+          if (i < M && act[i]) combine(o[i], r, vi, P.tol, err_row);
+        }
       }
     }
   };
-  if (tid == 0) {
-    rock_prepare(P, C, N, leafb);
-    __threadfence();
-  }
-  grid.sync();
-  refresh();
+  __syncthreads();
+  if (threadIdx.x == 0) rock_prepare(P, C, N, leafb);
+  __syncthreads();
+  bool first = true;
   for (int round = 0; round < 20000; round++) {
-    if (s_fin) break;
-    const int nmax = s_nmax;
-    double err[M];
+    if (C.finished) break;
+    double err[M], err_row = 0.0;  // err_row: the merged rows' share of species sub (+ G, ...)
 #pragma unroll
     for (int i = 0; i < M; i++) err[i] = 0.0;
-    // recurrence stages P_j -> W[(j-1) % 3]
-    for (int j = 1; j <= nmax; j++) {
-      sweep(j, err);
+    // stage 1: P_1 = y + kap_1 h L y (an operator sweep in the first step,
+    // then an axpy on the kept L y)
+    if (first) {
+      build_ops(kPhaseFinish + K_STAGE1);
+      sweep(err, err_row);
+    } else {
+      for (int i = 0; i < M; i++) {
+        if (C.done[i]) continue;
+        const double* tb = P.tab.data + P.tab.off[C.s[i]];
+        const double ca = tb[10], cl = tb[10 + 2 * C.n[i]] * C.h[i] * P.Dc[i];
+        const double *y = Y(i), *ly = LY(i);
+        double* out = Rb(i, 0);
+        for (int64_t r = tid; r < N; r += nth) out[r] = ca * y[r] + cl * ly[r];
+      }
+    }
+    first = false;
+    grid.sync();
+    // recurrence stages P_j -> R[(j-1) % 3]
+    for (int j = 2; j <= C.nmax; j++) {
+      build_ops(j);
+      sweep(err, err_row);
       grid.sync();
     }
     // Horner finishing procedure and the embedded estimate
     for (int mode = K_H3; mode <= K_FSAL; mode++) {
-      sweep(kPhaseFinish + mode, err);
+      build_ops(kPhaseFinish + mode);
+      sweep(err, err_row);
       if (mode == K_FSAL) {
 #pragma unroll
         for (int i = 0; i < M; i++) {
-          if (s_done[i]) continue;  // uniform across the grid
-          sh[threadIdx.x] = err[i];
+          if (C.done[i]) continue;  // uniform across the grid
+          sh[threadIdx.x] = err[i] + (i % G == sub ? err_row : 0.0);
           __syncthreads();
           for (int w = kBlock / 2; w > 0; w >>= 1) {
             if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
@@ -430,41 +468,43 @@ __global__ void __launch_bounds__(kBlock) k_rock_persistent(PersArgs P, const in
       }
       grid.sync();
     }
-    // control: block 0 reduces the per-block partial sums in a fixed order
-    // (strided by thread, then a tree), thread 0 accepts / rejects and sizes
+    // control, in every block: the per-block partial sums reduced in a fixed
+    // order (strided by thread, then a tree), then accept / reject and size
     // the next steps
-    __shared__ double s_err2[kMaxM];
-    if (blockIdx.x == 0) {
-      for (int i = 0; i < M; i++) {
-        if (s_done[i]) continue;
-        double v = 0.0;
-        for (int b = threadIdx.x; b < P.nb; b += blockDim.x) v += __ldcg(&P.part[i * P.nb + b]);
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = kBlock / 2; w > 0; w >>= 1) {
-          if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-          __syncthreads();
-        }
-        if (threadIdx.x == 0) s_err2[i] = sh[0];
+    for (int i = 0; i < M; i++) {
+      if (C.done[i]) continue;
+      double v = 0.0;
+      for (int b = threadIdx.x; b < P.nb; b += blockDim.x) v += __ldcg(&P.part[i * P.nb + b]);
+      sh[threadIdx.x] = v;
+      __syncthreads();
+      for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
       }
+      if (threadIdx.x == 0) s_err2[i] = sh[0];
+      __syncthreads();
     }
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
       for (int i = 0; i < M; i++) {
         C.acc_prev[i] = 0;
         if (C.done[i]) continue;
-        const double s2 = s_err2[i];
-        const double err = sqrt(s2 / (double)N);
-        C.err[i] = err;
-        if (!isfinite(err)) {
+        const double err2 = sqrt(s_err2[i] / (double)N);
+        C.err[i] = err2;
+        if (!isfinite(err2)) {
           C.status = MR_ENONFINITE;
           C.finished = 1;
           break;
         }
-        const double fac = err == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.8 * pow(err, -0.25)));
-        if (err <= 1.0) {
+        const double fac = err2 == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.8 * pow(err2, -0.25)));
+        if (err2 <= 1.0) {
+          // the candidate y_{n+1} (recurrence buffer (a+2) % 3) becomes the state
+          const int cp = (C.a[i] + 2) % 3;
+          const int t = s_py[i];
+          s_py[i] = s_pr[i][cp];
+          s_pr[i][cp] = t;
+          s_ly[i] ^= 1;
           C.acc_prev[i] = 1;
-          C.c_prev[i] = (C.a[i] + 2) % 3;
+          C.c_prev[i] = cp;
           C.t[i] = C.last[i] ? P.dt : C.t[i] + C.h[i];
           if (C.last[i]) C.done[i] = 1;
         } else {
@@ -474,17 +514,18 @@ __global__ void __launch_bounds__(kBlock) k_rock_persistent(PersArgs P, const in
       }
       C.rounds++;
       if (!C.finished) rock_prepare(P, C, N, leafb);
-      __threadfence();
     }
-    grid.sync();
-    refresh();
-    // accepted species: the new state replaces the old
-    for (int64_t r = tid; r < N; r += nth)
-      for (int i = 0; i < M; i++)
-        if (s_acc[i]) Up(i)[r] = Wp(s_cp[i], i)[r];
-    grid.sync();
+    __syncthreads();
   }
-  if (tid == 0 && !s_fin) C.status = MR_EROCK_STEP;
+  if (threadIdx.x == 0 && !C.finished) C.status = MR_EROCK_STEP;
+  // the final state back into the state array where a swap moved it
+  for (int i = 0; i < M; i++) {
+    if (s_py[i] == 0) continue;
+    const double* y = Y(i);
+    double* u = P.U + (int64_t)i * capL;
+    for (int64_t r = tid; r < N; r += nth) u[r] = y[r];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *P.ctl = C;
 }
 
 // ------------------------------------------------------------ host coefficients
@@ -812,15 +853,15 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   P.rho = c->rho;
   for (int i = 0; i < m; i++) P.Dc[i] = c->prob.D[i];
   P.U = c->tb[c->cur].U;
-  for (int q = 0; q < 4; q++) P.W[q] = c->work[q];
+  for (int q = 0; q < 6; q++) P.W[q] = c->work[q];
   P.part = c->red;
   P.ctl = dctl;
   IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_slot};
-  const int32_t* nbr = c->nbr;
-  const uint8_t* lvl = c->leaf_lvl;
+  const int4* reg = c->reg_tab;
   const int32_t* irr_leaf = c->irr_leaf;
   int64_t nirr = c->stats.irregular_rows;
-  void* args[] = {&P, (void*)&nbr, (void*)&lvl, &R, (void*)&irr_leaf, &nirr};
+  int64_t nreg = N - nirr;
+  void* args[] = {&P, (void*)&reg, &nreg, &R, (void*)&irr_leaf, &nirr};
   MR_CUDA(c, cudaEventRecord(c->tev[0], c->stream));
   MR_CUDA(c, cudaLaunchCooperativeKernel(kern, nb, kBlock, args, 0, c->stream));
   MR_CUDA(c, cudaEventRecord(c->tev[1], c->stream));
