@@ -475,15 +475,15 @@ template <int D>
 struct IrrCfg;
 template <>
 struct IrrCfg<2> {
-  static constexpr int kCells = 256, kSort = 128, kWarps = 4;
+  static constexpr int kCells = 256, kSort = kIrrSlot2, kWarps = 4;
 };
 template <>
 struct IrrCfg<3> {
-  static constexpr int kCells = 1024, kSort = 1024, kWarps = 2;
+  static constexpr int kCells = 1024, kSort = kIrrSlot3, kWarps = 2;
 };
 
 constexpr unsigned long long kEmptyCell = ~0ull;
-constexpr int32_t kAbsent = -1, kInternal = -2;
+constexpr int32_t kAbsent = -1, kInternal = -2, kUnresolved = -3;
 
 template <int D>
 struct IrrShared {
@@ -491,6 +491,7 @@ struct IrrShared {
   double w[IrrCfg<D>::kCells];
   int32_t st[IrrCfg<D>::kCells];  // leaf index, kAbsent or kInternal
   int16_t order[IrrCfg<D>::kCells];  // table slots in the order the cells were named
+  int16_t list[IrrCfg<D>::kCells];   // slots of the cells one pass expands
   int32_t skey[IrrCfg<D>::kSort];
   double sval[IrrCfg<D>::kSort];
   int n, cnt, lo, hi, bad;
@@ -501,9 +502,10 @@ struct IrrMaps {
   const int32_t* node_leaf;
 };
 
+// name a cell: shared memory only; its status (leaf, internal, absent) is
+// looked up afterwards for all the cells a pass named at once (resolve)
 template <int D>
-__device__ inline void cell_add(IrrShared<D>& S, const IrrMaps& M, const Level& L, int j, const int* k,
-                                double w) {
+__device__ inline void cell_add(IrrShared<D>& S, int j, const int* k, double w) {
   constexpr int kC = IrrCfg<D>::kCells;
   const uint32_t code = morton<D>(k);
   const unsigned long long key = ((unsigned long long)j << 48) | code;
@@ -511,8 +513,7 @@ __device__ inline void cell_add(IrrShared<D>& S, const IrrMaps& M, const Level& 
   for (int probe = 0; probe < kC; probe++) {
     const unsigned long long old = atomicCAS(&S.key[h], kEmptyCell, key);
     if (old == kEmptyCell) {
-      const int32_t idx = M.dmap[L.doff[j] + code];
-      S.st[h] = idx < 0 ? kAbsent : (M.node_leaf[idx] >= 0 ? M.node_leaf[idx] : kInternal);
+      S.st[h] = kUnresolved;
       const int pos = atomicAdd(&S.n, 1);
       S.order[pos] = (int16_t)h;
       atomicMin(&S.lo, j);
@@ -529,8 +530,23 @@ __device__ inline void cell_add(IrrShared<D>& S, const IrrMaps& M, const Level& 
   atomicExch(&S.bad, 1);
 }
 
+// status of the cells named in order[from, to): one lane per cell, the
+// direct-map and leaf-index loads of all of them in flight together
 template <int D>
-__global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
+__device__ inline void resolve(IrrShared<D>& S, const IrrMaps& M, const Level& L, int from, int to, int lane) {
+#pragma unroll 4
+  for (int e = from + lane; e < to; e += 32) {
+    const int h = S.order[e];
+    const unsigned long long key = S.key[h];
+    const int j = (int)(key >> 48);
+    const int32_t idx = M.dmap[L.doff[j] + (int64_t)(key & 0xffffffffffffull)];
+    const int32_t li = idx >= 0 ? M.node_leaf[idx] : -1;
+    S.st[h] = idx < 0 ? kAbsent : (li >= 0 ? li : kInternal);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
     k_irr_rows(const int32_t* __restrict__ irr_leaf, int64_t nrows, const int32_t* __restrict__ leaf_node,
                const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
                const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf, Level L, int slot,
@@ -570,8 +586,8 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
       if (q[a] >= 0 && q[a] < lim) {  // homogeneous Neumann: no flux through the boundary
         const int32_t idx = dmap[L.doff[j] + morton<D>(q)];
         if (idx < 0 || node_leaf[idx] >= 0) {
-          cell_add<D>(S, M, L, j, q, ih2);  // same-level leaf, or ghost by prediction
-          cell_add<D>(S, M, L, j, k, -ih2);
+          cell_add<D>(S, j, q, ih2);  // same-level leaf, or ghost by prediction
+          cell_add<D>(S, j, k, -ih2);
         } else {
           // finer side: minus the mean of the fluxes into the touching children
           for (int t = 0; t < (1 << D); t++) {
@@ -580,59 +596,82 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
             if (c[a] != 2 * q[a] + (sg > 0 ? 0 : 1)) continue;
             int g[3] = {c[0], c[1], c[2]};
             g[a] -= sg;
-            cell_add<D>(S, M, L, j + 1, g, -coef);
-            cell_add<D>(S, M, L, j + 1, c, coef);
+            cell_add<D>(S, j + 1, g, -coef);
+            cell_add<D>(S, j + 1, c, coef);
           }
         }
       }
     }
     __syncwarp();
-    // up: absent cells, finest level first
+    resolve<D>(S, M, L, 0, S.n, lane);
+    __syncwarp();
+    // gather the table slots of the cells at level jj with status st into
+    // S.list (ballot compaction, every lane in step); returns their count
+    auto gather = [&](int jj, int32_t want, int ne) {
+      int nl = 0;
+      for (int e0 = 0; e0 < ne; e0 += 32) {
+        const int e = e0 + lane;
+        int h = 0;
+        bool take = false;
+        if (e < ne) {
+          h = S.order[e];
+          take = (int)(S.key[h] >> 48) == jj && S.st[h] == want;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, take);
+        if (take) S.list[nl + __popc(b & ((1u << lane) - 1))] = (int16_t)h;
+        nl += __popc(b);
+      }
+      __syncwarp();
+      return nl;
+    };
+    // up: absent cells, finest level first; the (cell, stencil offset) pairs
+    // of a level are spread over the lanes
     // (the pass's bounds are read by every lane before any lane adds a cell)
+    constexpr int NST = D == 2 ? 9 : 27;
     for (int jj = S.hi;; jj--) {
       const bool go = jj >= 1 && jj >= S.lo && !S.bad;
       const int ne = S.n;
       __syncwarp();
       if (!go) break;
-      for (int e = lane; e < ne; e += 32) {
-        const int h = S.order[e];
-        if ((int)(S.key[h] >> 48) != jj || S.st[h] != kAbsent) continue;
+      const int nl = gather(jj, kAbsent, ne);
+      for (int it = lane; it < nl * NST; it += 32) {
+        const int h = S.list[it / NST];
         int c[3] = {0, 0, 0};
         unmorton<D>((uint32_t)(S.key[h] & 0xffffffffffffull), c);
-        const double wc = S.w[h];
-        constexpr int NST = D == 2 ? 9 : 27;
-        for (int o = 0; o < NST; o++) {
-          int oo = o, s[3] = {0, 0, 0};
-          double w = wc;
-          for (int a = 0; a < D; a++) {
-            const int off = oo % 3 - 1;
-            oo /= 3;
-            s[a] = mirror((c[a] >> 1) + off, jj - 1);
-            w *= wpred(c[a] & 1, off);
-          }
-          cell_add<D>(S, M, L, jj - 1, s, w);
+        int oo = it % NST, st[3] = {0, 0, 0};
+        double w = S.w[h];
+        for (int a = 0; a < D; a++) {
+          const int off = oo % 3 - 1;
+          oo /= 3;
+          st[a] = mirror((c[a] >> 1) + off, jj - 1);
+          w *= wpred(c[a] & 1, off);
         }
+        cell_add<D>(S, jj - 1, st, w);
       }
       __syncwarp();
+      resolve<D>(S, M, L, ne, S.n, lane);
+      __syncwarp();
     }
-    // down: internal cells, coarsest level first
+    // down: internal cells, coarsest level first, (cell, child) pairs over
+    // the lanes
     for (int jj = S.lo;; jj++) {
       const bool go = jj <= S.hi && !S.bad;
       const int ne = S.n;
       __syncwarp();
       if (!go) break;
-      for (int e = lane; e < ne; e += 32) {
-        const int h = S.order[e];
-        if ((int)(S.key[h] >> 48) != jj || S.st[h] != kInternal) continue;
+      const int nl = gather(jj, kInternal, ne);
+      for (int it = lane; it < (nl << D); it += 32) {
+        const int h = S.list[it >> D];
+        const int t = it & ((1 << D) - 1);
         int c[3] = {0, 0, 0};
         unmorton<D>((uint32_t)(S.key[h] & 0xffffffffffffull), c);
         const double w = S.w[h] * (1.0 / (1 << D));
-        for (int t = 0; t < (1 << D); t++) {
-          int ch[3] = {0, 0, 0};
-          for (int a = 0; a < D; a++) ch[a] = 2 * c[a] + ((t >> a) & 1);
-          cell_add<D>(S, M, L, jj + 1, ch, w);
-        }
+        int ch[3] = {0, 0, 0};
+        for (int a = 0; a < D; a++) ch[a] = 2 * c[a] + ((t >> a) & 1);
+        cell_add<D>(S, jj + 1, ch, w);
       }
+      __syncwarp();
+      resolve<D>(S, M, L, ne, S.n, lane);
       __syncwarp();
     }
     // collect the leaves with non-zero weight, then sort them by leaf index
@@ -650,39 +689,21 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps)
       }
     }
     __syncwarp();
+    // each entry's place in the row is its rank by leaf index (the leaves are
+    // distinct), so the row comes out sorted without a sort network; the
+    // absolute row sum is exact in any order (dyadic weights)
     const int cntr = min(S.cnt, kS);
-    int np2 = 1;
-    while (np2 < cntr) np2 <<= 1;
-    for (int q = cntr + lane; q < np2; q += 32) {
-      S.skey[q] = 0x7fffffff;
-      S.sval[q] = 0.0;
-    }
-    __syncwarp();
-    for (int size = 2; size <= np2; size <<= 1)
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int q = lane; q < np2; q += 32) {
-          const int p = q ^ stride;
-          if (p > q) {
-            const bool up = (q & size) == 0;
-            if ((S.skey[q] > S.skey[p]) == up) {
-              const int32_t tk = S.skey[q];
-              S.skey[q] = S.skey[p];
-              S.skey[p] = tk;
-              const double tv = S.sval[q];
-              S.sval[q] = S.sval[p];
-              S.sval[p] = tv;
-            }
-          }
-        }
-        __syncwarp();
-      }
     double sa = 0.0;
     const bool ok = !S.bad && cntr <= slot;
     for (int q = lane; q < cntr; q += 32) {
+      const int32_t kq = S.skey[q];
+      int rank = 0;
+#pragma unroll 8
+      for (int p = 0; p < cntr; p++) rank += S.skey[p] < kq;
       sa += fabs(S.sval[q]);
       if (ok) {
-        col[row * (int64_t)slot + q] = S.skey[q];
-        wout[row * (int64_t)slot + q] = S.sval[q];
+        col[row * (int64_t)slot + rank] = kq;
+        wout[row * (int64_t)slot + rank] = S.sval[q];
       }
     }
     for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
