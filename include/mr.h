@@ -51,7 +51,8 @@ typedef enum {
   MR_ERADAU_SINGULAR = -12,
   MR_EROCK_STEP = -20,
   MR_ENONFINITE = -30,
-  MR_ETIMEOUT = -40
+  MR_ETIMEOUT = -40,
+  MR_EIO = -50
 } mr_status;
 
 enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2 };
@@ -150,6 +151,20 @@ mr_status diffuse_rock4(mr_ctx *ctx, double dt, double tol);
 /* One Strang step: mr_adapt(eta); R_{dt/2}; D_dt; R_{dt/2}. */
 mr_status strang_step(mr_ctx *ctx, double dt, double eta, double rtol, double atol,
                       double rock_tol);
+
+/* Checkpoint and resume.  mr_save writes the current leaves to `path`:
+ * a 64-byte header (8-byte magic "MRGB300\0"; int32 format version 1, dim,
+ * J, jmin, m, model, precision, 0; int64 leaf count; 16 zero bytes), the model parameters
+ * and diffusion coefficients of the problem (8 + 16 doubles), the leaf keys
+ * (n uint64, the key layout above) and the values (m x n doubles, species
+ * major), all little-endian.  mr_load replaces the context's tree by the
+ * file's leaves; the file must have been written for the same dim, J, jmin,
+ * m and model (MR_EINVAL otherwise, the context unchanged).  MR_EIO if the
+ * file cannot be opened, written or read in full.  Resuming from a file gives
+ * the same results as continuing the saved context: the tree, its values and
+ * everything the next step computes from them are restored exactly. */
+mr_status mr_save(mr_ctx *ctx, const char *path);
+mr_status mr_load(mr_ctx *ctx, const char *path);
 
 mr_status mr_get_stats(const mr_ctx *ctx, mr_stats *out);
 

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "mr_internal.cuh"
 
@@ -214,6 +215,7 @@ const char* mr_status_str(mr_status s) {
     case MR_EROCK_STEP: return "ROCK4 step size underflow";
     case MR_ENONFINITE: return "non-finite value";
     case MR_ETIMEOUT: return "device wait timed out";
+    case MR_EIO: return "checkpoint file error";
   }
   return "unknown status";
 }
@@ -394,6 +396,92 @@ mr_status strang_step(mr_ctx* c, double dt, double eta, double rtol, double atol
   c->stats.ms_diffuse = d;
   refresh_tree_stats(c);
   return MR_OK;
+}
+
+namespace {
+struct SaveHeader {
+  char magic[8];
+  int32_t version, dim, J, jmin, m, model, precision, reserved;
+  int64_t n;
+  int64_t pad[2];
+};
+static_assert(sizeof(SaveHeader) == 64, "checkpoint header is 64 bytes");
+const char kMagic[8] = {'M', 'R', 'G', 'B', '3', '0', '0', '\0'};
+}  // namespace
+
+mr_status mr_save(mr_ctx* c, const char* path) {
+  if (check_ctx(c) || !path) return MR_EINVAL;
+  const int64_t N = c->tb[c->cur].nleaves;
+  std::vector<uint64_t> keys(N);
+  std::vector<double> vals((size_t)c->m * N);
+  int64_t n = 0;
+  mr_status s = mr_get_leaves(c, keys.data(), vals.data(), N, &n, 0);
+  if (s) return s;
+  SaveHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.dim = c->prob.dim;
+  h.J = c->prob.J;
+  h.jmin = c->prob.jmin;
+  h.m = c->m;
+  h.model = c->prob.model;
+  h.precision = c->prob.precision;
+  h.n = n;
+  FILE* f = fopen(path, "wb");
+  if (!f) {
+    c->last_error = "cannot open the checkpoint file for writing";
+    return MR_EIO;
+  }
+  bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(c->prob.params, sizeof(double), 8, f) == 8 &&
+            fwrite(c->prob.D, sizeof(double), 16, f) == 16 &&
+            fwrite(keys.data(), sizeof(uint64_t), n, f) == (size_t)n &&
+            fwrite(vals.data(), sizeof(double), (size_t)c->m * n, f) == (size_t)c->m * n;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) {
+    c->last_error = "checkpoint write failed";
+    return MR_EIO;
+  }
+  return MR_OK;
+}
+
+mr_status mr_load(mr_ctx* c, const char* path) {
+  if (check_ctx(c) || !path) return MR_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    c->last_error = "cannot open the checkpoint file";
+    return MR_EIO;
+  }
+  SaveHeader h;
+  double params[8], D[16];
+  bool ok = fread(&h, sizeof h, 1, f) == 1 && fread(params, sizeof(double), 8, f) == 8 &&
+            fread(D, sizeof(double), 16, f) == 16;
+  if (!ok) {
+    fclose(f);
+    c->last_error = "checkpoint header truncated";
+    return MR_EIO;
+  }
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) {
+    fclose(f);
+    c->last_error = "not a checkpoint of this library";
+    return MR_EINVAL;
+  }
+  if (h.dim != c->prob.dim || h.J != c->prob.J || h.jmin != c->prob.jmin || h.m != c->m ||
+      h.model != c->prob.model || h.n < 1 || h.n > c->cap_leaves) {
+    fclose(f);
+    c->last_error = "checkpoint was written for another problem";
+    return MR_EINVAL;
+  }
+  std::vector<uint64_t> keys(h.n);
+  std::vector<double> vals((size_t)c->m * h.n);
+  ok = fread(keys.data(), sizeof(uint64_t), h.n, f) == (size_t)h.n &&
+       fread(vals.data(), sizeof(double), (size_t)c->m * h.n, f) == (size_t)c->m * h.n;
+  fclose(f);
+  if (!ok) {
+    c->last_error = "checkpoint data truncated";
+    return MR_EIO;
+  }
+  return mr_set_leaves(c, h.n, keys.data(), vals.data(), 0);
 }
 
 mr_status mr_get_stats(const mr_ctx* c, mr_stats* out) {

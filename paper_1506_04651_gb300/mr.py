@@ -20,7 +20,7 @@ MAX_SPECIES, MAX_LEVEL = 16, 16
 
 STATUS = {0: "MR_OK", -1: "MR_EINVAL", -2: "MR_ENOMEM", -3: "MR_ECUDA", -4: "MR_ESTATE",
           -10: "MR_ERADAU_HMIN", -11: "MR_ERADAU_MAXSTEPS", -12: "MR_ERADAU_SINGULAR",
-          -20: "MR_EROCK_STEP", -30: "MR_ENONFINITE", -40: "MR_ETIMEOUT"}
+          -20: "MR_EROCK_STEP", -30: "MR_ENONFINITE", -40: "MR_ETIMEOUT", -50: "MR_EIO"}
 
 
 class Problem(C.Structure):
@@ -83,6 +83,8 @@ def lib():
             "mr_rock4_coefficients": [C.c_int, dp, dp, dp, dp, dp, C.POINTER(C.c_double)],
             "mr_last_error": [vp, C.c_char_p, C.c_size_t],
             "mr_fp64_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
+            "mr_save": [vp, C.c_char_p],
+            "mr_load": [vp, C.c_char_p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -204,6 +206,14 @@ class Context:
         self._check(lib().mr_get_complexity(self.h, C.c_void_p(out.ctypes.data), len(out), 0),
                     "mr_get_complexity")
         return out
+
+    def save(self, path):
+        """Write a checkpoint of the current leaves (mr_save)."""
+        self._check(lib().mr_save(self.h, os.fsencode(path)), "mr_save")
+
+    def load(self, path):
+        """Replace the tree by a checkpoint's leaves (mr_load)."""
+        self._check(lib().mr_load(self.h, os.fsencode(path)), "mr_load")
 
     def mass(self):
         out = np.zeros(self.m)
