@@ -12,7 +12,9 @@
  * polynomials) is recomputed here from its definition.
  *
  * Files:
- *   radau5.c  models f, J (Sec. 1 items I-II; BZ printed in Sec. 1) and the
+ *   radau5.c  models f, J (Sec. 1 items I-II; BZ printed in Sec. 1; a
+ *             synthetic stiff mass-action network standing in for the
+ *             paper's large-mechanism case, Sec. 1 item III) and the
  *             Radau5 reaction integrator (Sec. 2.1, App. A; algorithm of
  *             Hairer-Wanner, Solving ODEs II, Sec. IV.8, cited as MR1439506)
  *   rock4.c   ROCK4-type stabilized polynomials and the linear diffusion
@@ -33,8 +35,9 @@
 
 #define ORC_MAXM 16
 #define ORC_MAXL 16
+#define ORC_MAXR 32
 
-enum { ORC_MODEL_BZ = 1, ORC_MODEL_NAGUMO = 2, ORC_MODEL_LINEAR = 3 };
+enum { ORC_MODEL_BZ = 1, ORC_MODEL_NAGUMO = 2, ORC_MODEL_LINEAR = 3, ORC_MODEL_NETWORK = 4 };
 
 enum {
   ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESTATE = -4,
@@ -46,6 +49,11 @@ typedef struct {
   int kind, m;
   double p[8];                 /* BZ: eps, mu, f, q.  NAGUMO: k */
   double K[ORC_MAXM * ORC_MAXM]; /* LINEAR: f(u) = K u (row-major) */
+  /* NETWORK: nr reversible mass-action reactions u_a + u_b <-> u_c + u_d,
+   * species (a, b, c, d) = sp[r][0..3], rates kf[r] (forward), kb[r] */
+  int nr;
+  int sp[ORC_MAXR][4];
+  double kf[ORC_MAXR], kb[ORC_MAXR];
 } orc_model;
 
 typedef struct {

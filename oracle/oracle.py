@@ -21,8 +21,9 @@ _lock = threading.Lock()
 _lib = None
 
 OK = 0
-MODEL_BZ, MODEL_NAGUMO, MODEL_LINEAR = 1, 2, 3
+MODEL_BZ, MODEL_NAGUMO, MODEL_LINEAR, MODEL_NETWORK = 1, 2, 3, 4
 MAXM = 16
+MAXR = 32
 
 
 def build(force: bool = False) -> str:
@@ -42,7 +43,8 @@ def build(force: bool = False) -> str:
 
 class Model(C.Structure):
     _fields_ = [("kind", C.c_int), ("m", C.c_int), ("p", C.c_double * 8),
-                ("K", C.c_double * (MAXM * MAXM))]
+                ("K", C.c_double * (MAXM * MAXM)), ("nr", C.c_int),
+                ("sp", (C.c_int * 4) * MAXR), ("kf", C.c_double * MAXR), ("kb", C.c_double * MAXR)]
 
 
 class RadauStats(C.Structure):
@@ -142,6 +144,17 @@ def make_model(kind: str, m: int | None = None, params=None, K=None) -> Model:
         md.kind, md.m = MODEL_LINEAR, K.shape[0]
         for i, v in enumerate(K.ravel()):
             md.K[i] = v
+    elif kind == "network":
+        # params = (species (nr x 4 ints), kf (nr), kb (nr)); m species
+        sp, kf, kb = params
+        sp = np.asarray(sp, dtype=np.int64)
+        md.kind, md.m, md.nr = MODEL_NETWORK, int(m), len(sp)
+        assert md.nr <= MAXR and md.m <= MAXM
+        for r in range(md.nr):
+            for t in range(4):
+                md.sp[r][t] = int(sp[r, t])
+            md.kf[r] = float(kf[r])
+            md.kb[r] = float(kb[r])
     else:
         raise ValueError(kind)
     return md

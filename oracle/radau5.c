@@ -26,7 +26,11 @@
 /* BZ (Oregonator), Sec. 1 item II with a=u1, b=u2, c=u3:
  *   f_a = (-q a - a b + f c)/mu,  f_b = (b - b^2 + a (q - b))/eps,  f_c = b - c.
  * NAGUMO, Sec. 1 item I: f = k u^2 (1 - u).
- * LINEAR: f = K u (used only by the splitting-order pin). */
+ * LINEAR: f = K u (used only by the splitting-order pin).
+ * NETWORK: reversible mass-action reactions u_a + u_b <-> u_c + u_d with
+ *   rate w_r = kf_r u_a u_b - kb_r u_c u_d; each reaction removes w_r from
+ *   f_a and f_b and adds it to f_c and f_d (two molecules in, two out, so
+ *   sum_i f_i = 0). */
 void orc_model_f(const orc_model *md, const double *y, double *f) {
   if (md->kind == ORC_MODEL_BZ) {
     double eps = md->p[0], mu = md->p[1], ff = md->p[2], q = md->p[3];
@@ -37,6 +41,16 @@ void orc_model_f(const orc_model *md, const double *y, double *f) {
   } else if (md->kind == ORC_MODEL_NAGUMO) {
     double k = md->p[0], u = y[0];
     f[0] = k * u * u * (1.0 - u);
+  } else if (md->kind == ORC_MODEL_NETWORK) {
+    for (int i = 0; i < md->m; i++) f[i] = 0.0;
+    for (int r = 0; r < md->nr; r++) {
+      const int *s = md->sp[r];
+      double w = md->kf[r] * y[s[0]] * y[s[1]] - md->kb[r] * y[s[2]] * y[s[3]];
+      f[s[0]] -= w;
+      f[s[1]] -= w;
+      f[s[2]] += w;
+      f[s[3]] += w;
+    }
   } else {
     int m = md->m;
     for (int i = 0; i < m; i++) {
@@ -59,6 +73,20 @@ void orc_model_jac(const orc_model *md, const double *y, double *J) {
   } else if (md->kind == ORC_MODEL_NAGUMO) {
     double k = md->p[0], u = y[0];
     J[0] = k * (2.0 * u - 3.0 * u * u);
+  } else if (md->kind == ORC_MODEL_NETWORK) {
+    for (int q = 0; q < m * m; q++) J[q] = 0.0;
+    for (int r = 0; r < md->nr; r++) {
+      const int *s = md->sp[r];
+      /* d w_r / d u of the four species, in the order a, b, c, d */
+      double dw[4] = {md->kf[r] * y[s[1]], md->kf[r] * y[s[0]],
+                      -md->kb[r] * y[s[3]], -md->kb[r] * y[s[2]]};
+      for (int t = 0; t < 4; t++) {
+        J[s[0] * m + s[t]] -= dw[t];
+        J[s[1] * m + s[t]] -= dw[t];
+        J[s[2] * m + s[t]] += dw[t];
+        J[s[3] * m + s[t]] += dw[t];
+      }
+    }
   } else {
     memcpy(J, md->K, sizeof(double) * m * m);
   }

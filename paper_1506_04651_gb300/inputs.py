@@ -133,3 +133,48 @@ def batch_instances(n: int, master_seed: int = 2026):
         out.append(dict(seed=s, J=7 + int(r[0] * 4), f=0.9 + 1.1 * r[1],
                         eta=10.0 ** (-4.0 + 2.0 * r[2]), x0=0.2 + 0.6 * r[3]))
     return out
+
+
+def network_instance(seed: int = 5, m: int = 16, nr: int = 32):
+    """Synthetic stiff mass-action network: nr reversible reactions
+    u_a + u_b <-> u_c + u_d, the four species of each reaction distinct and
+    drawn uniformly, forward / backward rates log-uniform in [1e-2, 1e6],
+    diffusion coefficients log-uniform in [1e-4, 1e-2].  Returns
+    (species (nr x 4 int32), kf (nr), kb (nr), D (m))."""
+    r = uniform(seed, np.arange(4 * nr + 2 * nr + m + 64 * nr, dtype=np.uint64))
+    sp = np.zeros((nr, 4), dtype=np.int32)
+    pos = 0
+    for q in range(nr):
+        pool = list(range(m))
+        for t in range(4):
+            # draw without replacement: index into the remaining species
+            k = int(r[pos] * len(pool))
+            pos += 1
+            sp[q, t] = pool.pop(min(k, len(pool) - 1))
+    kf = 10.0 ** (-2.0 + 8.0 * r[pos:pos + nr])
+    pos += nr
+    kb = 10.0 ** (-2.0 + 8.0 * r[pos:pos + nr])
+    pos += nr
+    D = 10.0 ** (-4.0 + 2.0 * r[pos:pos + m])
+    return sp, kf, kb, D
+
+
+def network_bumps(d: int, J: int, seed: int = 5, m: int = 16, nbumps: int = 4):
+    """Positive initial state of the network workload: per species
+    u_i = 0.1 + sum_b A_ib exp(-|x - c_ib|^2 / (2 sigma_ib^2)), A ~ U[0.2, 1],
+    sigma ~ U[0.05, 0.15], centres ~ U[0.2, 0.8]^d; shape (m, 2^(dJ))."""
+    xs = cell_centres(d, J)
+    r = uniform(seed ^ 0x5EED, np.arange(m * nbumps * (2 + d), dtype=np.uint64)).reshape(m, nbumps, 2 + d)
+    u = np.empty((m, xs[0].size))
+    for i in range(m):
+        acc = np.full(xs[0].size, 0.1)
+        for b in range(nbumps):
+            amp = 0.2 + 0.8 * r[i, b, 0]
+            sig = 0.05 + 0.10 * r[i, b, 1]
+            d2 = np.zeros(xs[0].size)
+            for a in range(d):
+                c = 0.2 + 0.6 * r[i, b, 2 + a]
+                d2 += (xs[a] - c) ** 2
+            acc += amp * np.exp(-d2 / (2.0 * sig * sig))
+        u[i] = acc
+    return u
