@@ -55,22 +55,27 @@ typedef enum {
   MR_EIO = -50
 } mr_status;
 
-enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2 };
+enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2, MR_MODEL_NETWORK = 3 };
 enum { MR_FP64 = 0, MR_MIXED = 1 };
 
 #define MR_MAX_SPECIES 16
 #define MR_MAX_LEVEL 16
+#define MR_MAX_REACTIONS 32
 
 /*
  * Problem description (Sec. 1, Eq. thesystem).
  *   dim       d in {2, 3}
  *   J         finest level (Sec. 2.2); d*J <= 30
  *   jmin      no leaf is coarser than jmin (1 <= jmin <= J)
- *   m         number of species (BZ: 3, NAGUMO: 1)
+ *   m         number of species (BZ: 3, NAGUMO: 1, NETWORK: 2..16)
  *   model     MR_MODEL_BZ: params = (eps, mu, f, q) of
  *               f_a = (-q a - a b + f c)/mu, f_b = (b - b^2 + a (q - b))/eps, f_c = b - c
  *               (Sec. 1 item II; the paper prints q = 0.02)
  *             MR_MODEL_NAGUMO: params = (k) of f = k u^2 (1 - u) (Sec. 1 item I)
+ *             MR_MODEL_NETWORK: a stiff mass-action reaction network (a
+ *               synthetic stand-in for the paper's large-mechanism case, Sec.
+ *               1 item III); no params, the reactions are given by
+ *               mr_set_network before the first reaction sub-step
  *   D         m diffusion coefficients
  *   precision MR_FP64, or MR_MIXED: Radau5 factorises and solves its Newton
  *             systems in FP32 (residuals, error estimate, step control, state,
@@ -120,6 +125,15 @@ void mr_destroy(mr_ctx *ctx);
  * fastest; the full tree is projected (Sec. 2.2) and then adapted with
  * threshold eta until no family can be deleted (Sec. 3.1.2). */
 mr_status mr_build(mr_ctx *ctx, const double *u0, int on_device, double eta);
+
+/* Reactions of an MR_MODEL_NETWORK context: nr (1..MR_MAX_REACTIONS)
+ * reversible mass-action reactions u_a + u_b <-> u_c + u_d, species[4 r + t]
+ * = (a, b, c, d) of reaction r (four distinct indices in [0, m)), rates
+ * kf[r], kb[r] >= 0:  w_r = kf_r u_a u_b - kb_r u_c u_d, f_a -= w_r,
+ * f_b -= w_r, f_c += w_r, f_d += w_r.  Host arrays, copied.  MR_EINVAL for
+ * another model or bad data. */
+mr_status mr_set_network(mr_ctx *ctx, int nr, const int32_t *species, const double *kf,
+                         const double *kb);
 
 /* Replace the tree by the n given leaves (keys as above, values m x n).
  * MR_EINVAL unless they tile the domain as a graded tree whose levels below

@@ -237,6 +237,8 @@ mr_status mr_create(const mr_problem* p, void* stream, mr_ctx** out) {
     if (!(p->params[0] > 0) || !(p->params[1] > 0)) return MR_EINVAL;
   } else if (p->model == MR_MODEL_NAGUMO) {
     if (p->m != 1 || p->nparams < 1) return MR_EINVAL;
+  } else if (p->model == MR_MODEL_NETWORK) {
+    if (p->m < 2 || p->m > kMaxM) return MR_EINVAL;
   } else {
     return MR_EINVAL;
   }
@@ -305,6 +307,34 @@ mr_status mr_build(mr_ctx* c, const double* u0, int on_device, double eta) {
   }
   if (!s) refresh_tree_stats(c);
   return s;
+}
+
+mr_status mr_set_network(mr_ctx* c, int nr, const int32_t* species, const double* kf, const double* kb) {
+  if (check_ctx(c) || c->prob.model != MR_MODEL_NETWORK || nr < 1 || nr > kMaxR || !species || !kf || !kb)
+    return MR_EINVAL;
+  NetModel N;
+  memset(&N, 0, sizeof N);
+  N.m = c->m;
+  N.nr = nr;
+  for (int r = 0; r < nr; r++) {
+    if (!(kf[r] >= 0.0) || !(kb[r] >= 0.0) || !isfinite(kf[r]) || !isfinite(kb[r])) return MR_EINVAL;
+    for (int t = 0; t < 4; t++) {
+      const int32_t a = species[4 * r + t];
+      if (a < 0 || a >= c->m) return MR_EINVAL;
+      for (int u = 0; u < t; u++)
+        if (species[4 * r + u] == a) return MR_EINVAL;
+      N.sp[r][t] = (int8_t)a;
+      if (t < 2)
+        N.neg[a] |= 1u << r;
+      else
+        N.pos[a] |= 1u << r;
+    }
+    N.kf[r] = kf[r];
+    N.kb[r] = kb[r];
+  }
+  c->net = N;
+  c->net_set = true;
+  return MR_OK;
 }
 
 mr_status mr_set_leaves(mr_ctx* c, int64_t n, const uint64_t* keys, const double* values, int on_device) {

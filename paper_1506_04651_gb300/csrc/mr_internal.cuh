@@ -24,6 +24,17 @@ namespace mrg {
 
 constexpr int kMaxL = MR_MAX_LEVEL;
 constexpr int kMaxM = MR_MAX_SPECIES;
+constexpr int kMaxR = MR_MAX_REACTIONS;
+
+// reactions of a network model as the kernels take them: species of every
+// reaction and, per species, the reactions that consume (neg) or produce
+// (pos) it as bit masks
+struct NetModel {
+  int m, nr;
+  int8_t sp[kMaxR][4];
+  double kf[kMaxR], kb[kMaxR];
+  uint32_t neg[kMaxM], pos[kMaxM];
+};
 constexpr int kBlock = 256;
 // merged operator rows at level jumps: entries per row (slot) by dimension
 constexpr int kIrrSlot2 = 128, kIrrSlot3 = 640;
@@ -114,6 +125,8 @@ struct TreeBuf {
 
 struct mr_ctx {
   mr_problem prob;
+  mrg::NetModel net;                 // MR_MODEL_NETWORK reactions
+  bool net_set = false;
   int d, J, jmin, m;
   cudaStream_t stream;
   int64_t n_level[mrg::kMaxL + 1];   // 2^(d j)

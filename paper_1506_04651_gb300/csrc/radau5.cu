@@ -22,19 +22,10 @@
 #include <string.h>
 
 #include "mr_internal.cuh"
+#include "radau_common.cuh"
 
 namespace mrg {
 namespace {
-
-struct RadauC {
-  double c1, c2;
-  double T[9], Ti[9];
-  double gam, alp, bet;
-  double ge[3];        // gam * e_j (embedded estimate weights times gam)
-  double idn[4][4];    // 1 / (nd[a] - nd[b]) for the nodes (0, c1, c2, 1)
-  double rt, at, fnewt;  // transformed tolerances and Newton tolerance (per call)
-  double fac[8];       // min(0.9, 0.9 (1 + 2 kmax)/(k + 2 kmax)), k Newton iterations
-};
 
 // Models hold reciprocals of their time scales so that a right-hand side is
 // multiplications only (FP64 division is an instruction sequence on the
@@ -69,9 +60,6 @@ struct Nagumo {
   __device__ void jac(const double* y, double* J) const { J[0] = k * (2.0 * y[0] - 3.0 * y[0] * y[0]); }
 };
 
-struct CellCount {
-  int nfev, njac, nstep, naccept, nreject, nnewton, ndec;
-};
 
 // LU with partial pivoting; the reciprocal of each pivot is kept so that the
 // solves only multiply
@@ -214,10 +202,6 @@ __device__ inline void sol_cplx(const T* ar, const T* ai, const int* piv, const 
   }
 }
 
-__device__ inline double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
-
-// x^(1/4) through two square roots (hardware-assisted) instead of pow
-__device__ inline double root4(double x) { return sqrt(sqrt(x)); }
 
 // One thread integrates one cell at a time; the kernel is persistent and its
 // threads pull cells from a device work queue.  The per-cell integration is
@@ -628,6 +612,8 @@ void solve3(double* a, double* b) {  // Gaussian elimination, partial pivoting
   }
 }
 
+}  // namespace
+
 // kernel-side constants: rc[0..1] = c1, c2; rc[2..10] T; rc[11..19] T^{-1};
 // rc[20..22] gam, alp, bet; rc[23..25] gam*e_j
 RadauC constants_from(const double* rc) {
@@ -650,7 +636,6 @@ RadauC constants_from(const double* rc) {
   return C;
 }
 
-}  // namespace
 
 // Radau IIA (s = 3) constants: nodes = zeros of the Radau right polynomial,
 // A from the collocation conditions sum_j a_ij c_j^(k-1) = c_i^k / k, the
@@ -753,6 +738,7 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   C.rt = 0.1 * pow(rtol, 2.0 / 3.0);
   C.at = C.rt * (atol / rtol);
   C.fnewt = std::max(10.0 * 1e-16 / C.rt, std::min(0.03, sqrt(C.rt)));
+  if (c->prob.model == MR_MODEL_NETWORK) return react_network(c, C, dt);
   MR_CUDA(c, cudaMemsetAsync(c->dc->radau, 0, sizeof(c->dc->radau), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->work_next, 0, sizeof(int), c->stream));

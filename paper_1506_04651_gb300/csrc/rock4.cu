@@ -269,7 +269,7 @@ __device__ inline void combine(const Ops& o, int64_t r, double Lx, double tol, d
 }
 
 template <int D, int M>
-__global__ void __launch_bounds__(kBlock, 2) k_rock_persistent(PersArgs P, const int4* __restrict__ reg, int64_t nreg,
+__global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersArgs P, const int4* __restrict__ reg, int64_t nreg,
                                                             IrrRows R, const int32_t* __restrict__ irr_leaf,
                                                             int64_t nirr) {
   namespace cg = cooperative_groups;
@@ -355,9 +355,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_persistent(PersArgs P, const
   // table (neighbour indices loaded once for all species), merged rows four
   // lanes each
   constexpr int G = 4;
-  static_assert(M <= G, "one merged-row lane per species");
+  constexpr int MG = (M + G - 1) / G;  // species a merged-row lane finishes
   const int sub = lane & (G - 1);
-  auto sweep = [&](double* err, double& err_row) {
+  auto sweep = [&](double* err, double* err_row) {
     const Ops* o = s_ops;
     const int* act = s_act;
     for (int64_t q = tid; q < nreg; q += nth) {
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_persistent(PersArgs P, const
 #pragma unroll
           for (int u = 1; u < G; u++)
             if (i0 + u < M && sub == u) vi = v[i0 + u];
-          if (i < M && act[i]) combine(o[i], r, vi, P.tol, err_row);
+          if (i < M && act[i]) combine(o[i], r, vi, P.tol, err_row[i0 / G]);
         }
       }
     }
@@ -422,9 +422,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_persistent(PersArgs P, const
   bool first = true;
   for (int round = 0; round < 20000; round++) {
     if (C.finished) break;
-    double err[M], err_row = 0.0;  // err_row: the merged rows' share of species sub (+ G, ...)
+    double err[M], err_row[MG];  // err_row[q]: the merged rows' share of species q G + sub
 #pragma unroll
     for (int i = 0; i < M; i++) err[i] = 0.0;
+#pragma unroll
+    for (int q = 0; q < MG; q++) err_row[q] = 0.0;
     // stage 1: P_1 = y + kap_1 h L y (an operator sweep in the first step,
     // then an axpy on the kept L y)
     if (first) {
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_persistent(PersArgs P, const
 #pragma unroll
         for (int i = 0; i < M; i++) {
           if (C.done[i]) continue;  // uniform across the grid
-          sh[threadIdx.x] = err[i] + (i % G == sub ? err_row : 0.0);
+          sh[threadIdx.x] = err[i] + (i % G == sub ? err_row[i / G] : 0.0);
           __syncthreads();
           for (int w = kBlock / 2; w > 0; w >>= 1) {
             if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
@@ -823,12 +825,14 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   int dev = 0, nsm = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (m != 1 && m != 3) {
-    c->last_error = "diffusion is built for 1 or 3 species";
-    return MR_EINVAL;
-  }
-  const void* kern = c->d == 2 ? (m == 3 ? (const void*)k_rock_persistent<2, 3> : (const void*)k_rock_persistent<2, 1>)
-                               : (m == 3 ? (const void*)k_rock_persistent<3, 3> : (const void*)k_rock_persistent<3, 1>);
+  // kernels for 1, 3 and up to 16 species (unused species of the 16-wide
+  // kernel are marked done)
+  const int M = m == 1 ? 1 : (m == 3 ? 3 : 16);
+  const void* kern =
+      c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1>
+                          : (M == 3 ? (const void*)k_rock_persistent<2, 3> : (const void*)k_rock_persistent<2, 16>))
+                : (M == 1 ? (const void*)k_rock_persistent<3, 1>
+                          : (M == 3 ? (const void*)k_rock_persistent<3, 3> : (const void*)k_rock_persistent<3, 16>));
   MR_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return MR_ECUDA;
   // enough blocks to cover the leaves, at most what is co-resident
@@ -837,9 +841,9 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   const int nb = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 2));
   RockCtl hctl;
   memset(&hctl, 0, sizeof hctl);
-  for (int i = 0; i < m; i++) {
+  for (int i = 0; i < kMaxM; i++) {
     hctl.h[i] = dt;
-    hctl.done[i] = !(dt > 0.0) || c->prob.D[i] == 0.0 || N == 0;
+    hctl.done[i] = i >= m || !(dt > 0.0) || c->prob.D[i] == 0.0 || N == 0;
   }
   RockCtl* dctl = reinterpret_cast<RockCtl*>(c->rock_ctl);
   MR_CUDA(c, cudaMemcpyAsync(dctl, &hctl, sizeof hctl, cudaMemcpyHostToDevice, c->stream));

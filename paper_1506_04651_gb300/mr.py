@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 MR_OK = 0
-MR_MODEL_BZ, MR_MODEL_NAGUMO = 1, 2
+MR_MODEL_BZ, MR_MODEL_NAGUMO, MR_MODEL_NETWORK = 1, 2, 3
 MR_FP64, MR_MIXED = 0, 1
 MAX_SPECIES, MAX_LEVEL = 16, 16
 
@@ -84,6 +84,7 @@ def lib():
             "mr_last_error": [vp, C.c_char_p, C.c_size_t],
             "mr_fp64_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
             "mr_save": [vp, C.c_char_p],
+            "mr_set_network": [vp, C.c_int, vp, dp, dp],
             "mr_load": [vp, C.c_char_p],
         }
         for name, args in sig.items():
@@ -122,6 +123,10 @@ def problem(dim, J, model="bz", params=None, D=None, jmin=2, precision=MR_FP64, 
         p.model, p.m = MR_MODEL_NAGUMO, 1
         params = params if params is not None else (10.0,)
         D = D if D is not None else (0.1,)
+    elif model == "network":
+        # reactions are set on the context (Context.set_network); D has m entries
+        p.model, p.m = MR_MODEL_NETWORK, len(D)
+        params = ()
     else:
         raise ValueError(model)
     p.nparams = len(params)
@@ -206,6 +211,14 @@ class Context:
         self._check(lib().mr_get_complexity(self.h, C.c_void_p(out.ctypes.data), len(out), 0),
                     "mr_get_complexity")
         return out
+
+    def set_network(self, species, kf, kb):
+        """Reactions of a network-model context (mr_set_network)."""
+        sp = np.ascontiguousarray(species, dtype=np.int32)
+        kf = np.ascontiguousarray(kf, dtype=np.float64)
+        kb = np.ascontiguousarray(kb, dtype=np.float64)
+        self._check(lib().mr_set_network(self.h, len(sp), C.c_void_p(sp.ctypes.data), C.c_void_p(kf.ctypes.data),
+                                         C.c_void_p(kb.ctypes.data)), "mr_set_network")
 
     def save(self, path):
         """Write a checkpoint of the current leaves (mr_save)."""
