@@ -47,6 +47,12 @@ WORKLOADS = {
     "bz3d_J7_eta1e-2": dict(d=3, J=7, eta=1e-2, dt=1e-3, gen="sphere", seed=3,
                             desc="3D BZ, J=7 (128^3 finest), eta=1e-2, spherical front r=0.3, "
                                  "w=0.02 + smooth seeded noise, dt=1e-3, FP64"),
+    "net3d_J8_eta1e-3": dict(d=3, J=8, eta=1e-3, dt=1e-3, gen="network", seed=5, model="network",
+                             oracle_J=4,
+                             desc="3D stiff mass-action network, 16 species, 32 reversible reactions "
+                                  "A+B<->C+D (seeded species, rates log-U[1e-2,1e6], D log-U[1e-4,1e-2]), "
+                                  "J=8 (256^3 finest), eta=1e-3, Gaussian-bump initial state, dt=1e-3, "
+                                  "Radau5 on 48x48 Newton systems, FP64"),
 }
 BATCH = {"batch64_bz2d": dict(n=64, dt=1e-3,
                               desc="64 independent 2D BZ instances, seeded J ~ U{7..10}, f ~ U[0.9, 2.0], "
@@ -57,13 +63,54 @@ DEFAULT = "bz2d_J10_eta1e-3"
 TOL = 1e-6
 
 
-def initial_state(w):
+def initial_state(w, J=None):
     from paper_1506_04651_gb300 import inputs as I
+    J = J or w["J"]
+    if w["gen"] == "network":
+        return I.network_bumps(w["d"], J, w["seed"])
     if w["gen"] == "cross":
-        return I.bz_cross_2d(w["J"], w["seed"], w=w.get("w", 0.02), amp=w.get("amp", 0.01))
+        return I.bz_cross_2d(J, w["seed"], w=w.get("w", 0.02), amp=w.get("amp", 0.01))
     if w["gen"] == "front":
-        return I.bz_front_2d(w["J"], w["seed"])
-    return I.bz_sphere_3d(w["J"], w["seed"])
+        return I.bz_front_2d(J, w["seed"])
+    return I.bz_sphere_3d(J, w["seed"])
+
+
+def make_context(mr, w, stream, precision=0):
+    """A library context for workload w (BZ, or the network with its reactions set)."""
+    from paper_1506_04651_gb300 import inputs as I
+    if w.get("model") == "network":
+        sp, kf, kb, D = I.network_instance(w["seed"])
+        c = mr.Context(mr.problem(w["d"], w["J"], model="network", D=D, precision=precision), stream=stream)
+        c.set_network(sp, kf, kb)
+        return c
+    return mr.Context(mr.problem(w["d"], w["J"], precision=precision), stream=stream)
+
+
+def oracle_model(w):
+    """(oracle model, diffusion coefficients, species) of workload w."""
+    from oracle import oracle as O
+    from paper_1506_04651_gb300 import inputs as I
+    if w.get("model") == "network":
+        sp, kf, kb, D = I.network_instance(w["seed"])
+        return O.make_model("network", m=16, params=(sp, kf, kb)), D, 16
+    return O.make_model("bz"), I.BZ_D, 3
+
+
+def moiety_basis(w):
+    """Rows: a basis of the conserved moieties of the network (left null space
+    of the stoichiometric matrix) and the total amount; None for BZ."""
+    from paper_1506_04651_gb300 import inputs as I
+    if w.get("model") != "network":
+        return None
+    sp = I.network_instance(w["seed"])[0]
+    S = np.zeros((16, len(sp)))
+    for r, (a, b, c, d) in enumerate(sp):
+        S[a, r] -= 1
+        S[b, r] -= 1
+        S[c, r] += 1
+        S[d, r] += 1
+    _, sv, Vt = np.linalg.svd(S.T)
+    return np.vstack([Vt[int((sv > 1e-10).sum()):], np.ones(16)])
 
 
 def profiled_traffic(kernel_file, summary):
@@ -149,15 +196,15 @@ def cpu_oracle_rate(w, u0, budget_s=20.0, max_steps=100):
     """The oracle as it stands (single-threaded C), Strang steps on the same
     workload until the time budget is spent; returns (rate, steps, cores)."""
     from oracle import oracle as O
-    from paper_1506_04651_gb300 import inputs as I
-    T = O.Tree(w["d"], w["J"], 3, jmin=2)
+    md, D, m = oracle_model(w)
+    J = w.get("oracle_J", w["J"])
+    T = O.Tree(w["d"], J, m, jmin=2)
     T.set_full(u0)
     assert T.adapt(w["eta"]) == 0
-    md = O.make_model("bz")
     leaves, t_tot, steps = 0, 0.0, 0
     while steps < max_steps and t_tot < budget_s:
         t0 = time.perf_counter()
-        rc = T.strang(md, I.BZ_D, w["dt"], w["eta"], TOL, TOL, TOL)
+        rc = T.strang(md, D, w["dt"], w["eta"], TOL, TOL, TOL)
         t_tot += time.perf_counter() - t0
         assert rc == 0, rc
         leaves += T.num_leaves()
@@ -169,10 +216,14 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    u0 = initial_state(w)
+    oj = w.get("oracle_J", w["J"])
+    u0 = initial_state(w, oj)
     budget = min(240.0, 20.0 + 2.0 * args.steps)
     rate, steps, cores = cpu_oracle_rate(w, u0, budget_s=budget, max_steps=args.steps)
-    sample = f"first {steps} Strang steps of the workload from its initial grid (single-threaded C oracle)"
+    sample = (f"first {steps} Strang steps of the workload from its initial grid (single-threaded C oracle)"
+              if oj == w["J"] else
+              f"first {steps} Strang steps of the same problem at finest level J={oj} instead of {w['J']} "
+              f"(single-threaded C oracle; the full size takes minutes per step)")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
             "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -198,8 +249,9 @@ def run_gpu(args, w):
         pg = dist
     stream = torch.cuda.current_stream()
     u0 = initial_state(w)
-    ctx = mr.Context(mr.problem(w["d"], w["J"]), stream=stream)
+    ctx = make_context(mr, w, stream)
     ctx.build(torch.from_numpy(u0).to(dev), w["eta"])
+    basis = moiety_basis(w)
 
     def step():
         ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
@@ -209,25 +261,38 @@ def run_gpu(args, w):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # the state at the start of the timed region, kept on the host: the
+    # end-to-end measurement replays the same steps from it
+    k_start, v_start = ctx.leaves()
+    mass0 = ctx.mass()
     st0 = ctx.stats()
     clocks = ClockSampler(local)
     clocks.start()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    leaves = 0
+    leaves, nmax = 0, len(k_start)
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record(stream)
         step()
         ev1[k].record(stream)
-        leaves += ctx.stats()["leaves"]
+        nk = ctx.stats()["leaves"]
+        leaves += nk
+        nmax = max(nmax, nk)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     clk = clocks.stop()
     st1 = ctx.stats()
+    mass1 = ctx.mass()
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    conservation = None
+    if basis is not None:
+        y0, y1 = basis @ mass0, basis @ mass1
+        conservation = {"total_amount_rel_drift": float(abs(y1[-1] - y0[-1]) / abs(y0[-1])),
+                        "moiety_max_drift_rel_to_total": float(np.max(np.abs(y1 - y0)) / abs(y0[-1])),
+                        "moieties": int(len(basis)), "steps": args.steps}
     if pg:
         t = torch.tensor([ms], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -252,7 +317,9 @@ def run_gpu(args, w):
     hbm = peaks.get("hbm_gbs")
     if rad_ms >= rock_ms:
         ach = rad_fl / (rad_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_radau (Radau5, FP64)", "achieved": ach, "peak": fp64_tf,
+        kname = ("k_radau_team (Radau5, one 16-lane team per cell, FP64)" if w.get("model") == "network"
+                 else "k_radau (Radau5, FP64)")
+        roof = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": fp64_tf,
                 "unit": "TFLOP/s", "frac": ach / fp64_tf,
                 "traffic": profiled_traffic("radau5.cu", "k_radau_bz2d_J10.md")
                 if args.workload == DEFAULT else None,
@@ -273,35 +340,40 @@ def run_gpu(args, w):
                "last_step_phase_ms": {"adapt_and_tables": st1["ms_adapt"], "react_both_halves": st1["ms_react"],
                                       "diffuse": st1["ms_diffuse"]}}
 
-    # end to end through the C-ABI with host buffers: state in from pinned host
-    # memory, one step, state out, every step
-    n0 = ctx.num_leaves()
-    cap = 1 << (w["d"] * w["J"])
+    # end to end through the C-ABI with host buffers, replaying the timed
+    # steps from the same starting state: every step the state goes in from
+    # pinned host memory, the step runs, the state comes out
+    m = ctx.m
+    cap = nmax
     hk = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
-    hv = torch.empty(3 * cap, dtype=torch.float64, pin_memory=True).numpy()
+    hv = torch.empty(m * cap, dtype=torch.float64, pin_memory=True).numpy()
     hk2 = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
-    hv2 = torch.empty(3 * cap, dtype=torch.float64, pin_memory=True).numpy()
-    keys, vals = ctx.leaves(hk[:n0], hv[:3 * n0].reshape(3, n0))
-    n_e2e = min(args.steps, 20)
+    hv2 = torch.empty(m * cap, dtype=torch.float64, pin_memory=True).numpy()
+    n0 = len(k_start)
+    keys, vals = hk[:n0], hv[:m * n0].reshape(m, n0)
+    keys[:] = k_start
+    vals[:] = v_start
+    del k_start, v_start
+    n_e2e = args.steps
     h2d = d2h = 0
     e2e_leaves = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(n_e2e):
-        n = len(keys)
         ctx.set_leaves(keys, vals)
         h2d += keys.nbytes + vals.nbytes
         step()
         n = ctx.num_leaves()
         e2e_leaves += n
-        keys, vals = ctx.leaves(hk2[:n], hv2[:3 * n].reshape(3, n))
+        keys, vals = ctx.leaves(hk2[:n], hv2[:m * n].reshape(m, n))
         d2h += keys.nbytes + vals.nbytes
         hk, hk2, hv, hv2 = hk2, hk, hv2, hv
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     e2e = {"value": e2e_leaves / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
            "d2h_bytes_per_step": d2h // n_e2e, "steps": n_e2e,
-           "note": "mr_set_leaves(host) + strang_step + mr_get_leaves(host) per step, wall clock"}
+           "note": "the timed steps replayed from the same starting state: mr_set_leaves(host) + "
+                   "strang_step + mr_get_leaves(host) per step, wall clock"}
 
     # mixed form (FP32 Newton factorisations in Radau5) on the same workload and
     # the same number of steps from the same initial grid; its final state is
@@ -317,9 +389,12 @@ def run_gpu(args, w):
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        rate, steps, cores = cpu_oracle_rate(w, initial_state(w), budget_s=20.0, max_steps=50)
+        oj = w.get("oracle_J", w["J"])
+        rate, steps, cores = cpu_oracle_rate(w, initial_state(w, oj), budget_s=20.0, max_steps=50)
+        where = ("the same workload" if oj == w["J"] else
+                 f"the same problem at finest level J={oj} (the full size takes minutes per oracle step)")
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {steps} Strang steps of the same workload from its initial grid "
+               "sample": f"first {steps} Strang steps of {where} from its initial grid "
                          f"(single-threaded C oracle, ~20 s budget)"}
     st = ctx.stats()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -332,6 +407,8 @@ def run_gpu(args, w):
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "mixed": mixed,
             "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
+    if conservation:
+        line["conservation"] = conservation
     print(json.dumps(line), flush=True)
     ctx.close()
     if pg:
@@ -361,7 +438,7 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
     nsteps = args.warmup + args.steps
     res = {}
     for prec in (mr.MR_FP64, mr.MR_MIXED):
-        c = mr.Context(mr.problem(w["d"], w["J"], precision=prec), stream=stream)
+        c = make_context(mr, w, stream, precision=prec)
         c.build(torch.from_numpy(u0).to(dev), w["eta"])
         for _ in range(args.warmup):
             c.strang(w["dt"], w["eta"], TOL, TOL, TOL)
@@ -378,9 +455,17 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
         keys, vals = c.leaves()
         res[prec] = (leaves / (ms * 1e-3), ms / args.steps, keys, vals)
         c.close()
-    f64 = finest_grid(res[mr.MR_FP64][2], res[mr.MR_FP64][3], w["d"], w["J"])
-    mix = finest_grid(res[mr.MR_MIXED][2], res[mr.MR_MIXED][3], w["d"], w["J"])
-    err = max(float(np.sum(np.abs(mix[i] - f64[i])) / np.sum(np.abs(f64[i]))) for i in range(len(f64)))
+    kf, vf = res[mr.MR_FP64][2], res[mr.MR_FP64][3]
+    km, vm = res[mr.MR_MIXED][2], res[mr.MR_MIXED][3]
+    if np.array_equal(kf, km):
+        # same grid: the finest-grid L1 norm is the leaf sum weighted by the
+        # number of finest cells each leaf covers
+        vol = np.ldexp(1.0, (w["d"] * (w["J"] - (kf >> np.uint64(48)).astype(np.int64))).astype(np.int32))
+        err = max(float(np.sum(vol * np.abs(vm[i] - vf[i])) / np.sum(vol * np.abs(vf[i]))) for i in range(len(vf)))
+    else:
+        f64 = finest_grid(kf, vf, w["d"], w["J"])
+        mix = finest_grid(km, vm, w["d"], w["J"])
+        err = max(float(np.sum(np.abs(mix[i] - f64[i])) / np.sum(np.abs(f64[i]))) for i in range(len(f64)))
     return {"value": res[mr.MR_MIXED][0], "ms_per_step": res[mr.MR_MIXED][1],
             "fp64_value_same_run": res[mr.MR_FP64][0], "speedup_vs_fp64": res[mr.MR_MIXED][0] / res[mr.MR_FP64][0],
             "rel_l1_vs_fp64_path": err, "steps": nsteps,

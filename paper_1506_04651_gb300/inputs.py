@@ -163,18 +163,21 @@ def network_bumps(d: int, J: int, seed: int = 5, m: int = 16, nbumps: int = 4):
     """Positive initial state of the network workload: per species
     u_i = 0.1 + sum_b A_ib exp(-|x - c_ib|^2 / (2 sigma_ib^2)), A ~ U[0.2, 1],
     sigma ~ U[0.05, 0.15], centres ~ U[0.2, 0.8]^d; shape (m, 2^(dJ))."""
-    xs = cell_centres(d, J)
+    n = 1 << J
+    x = (np.arange(n) + 0.5) / n
     r = uniform(seed ^ 0x5EED, np.arange(m * nbumps * (2 + d), dtype=np.uint64)).reshape(m, nbumps, 2 + d)
-    u = np.empty((m, xs[0].size))
+    u = np.empty((m,) + (n,) * d)
     for i in range(m):
-        acc = np.full(xs[0].size, 0.1)
+        acc = u[i]
+        acc.fill(0.1)
         for b in range(nbumps):
             amp = 0.2 + 0.8 * r[i, b, 0]
             sig = 0.05 + 0.10 * r[i, b, 1]
-            d2 = np.zeros(xs[0].size)
-            for a in range(d):
-                c = 0.2 + 0.6 * r[i, b, 2 + a]
-                d2 += (xs[a] - c) ** 2
-            acc += amp * np.exp(-d2 / (2.0 * sig * sig))
-        u[i] = acc
-    return u
+            # the Gaussian is the product of one factor per axis; array axes
+            # are (z, y, x) / (y, x) so that x varies fastest
+            g = [np.exp(-((x - (0.2 + 0.6 * r[i, b, 2 + a])) ** 2) / (2.0 * sig * sig)) for a in range(d)]
+            prod = amp * g[d - 1]
+            for a in range(d - 2, -1, -1):
+                prod = np.multiply.outer(prod, g[a])
+            acc += prod
+    return u.reshape(m, -1)
