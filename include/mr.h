@@ -78,8 +78,9 @@ enum { MR_FP64 = 0, MR_MIXED = 1 };
  *               mr_set_network before the first reaction sub-step
  *   D         m diffusion coefficients
  *   precision MR_FP64, or MR_MIXED: Radau5 factorises and solves its Newton
- *             systems in FP32 (residuals, error estimate, step control, state,
- *             diffusion, details and mass stay FP64)
+ *             systems in FP32 and the ROCK4 stages run on FP32 vectors
+ *             (Radau5 residuals, both error norms, step control, the state
+ *             between sub-steps, details and mass stay FP64)
  *   max_leaves leaf capacity; 0 means 2^(d J)
  */
 typedef struct {

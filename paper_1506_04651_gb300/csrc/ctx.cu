@@ -89,6 +89,7 @@ mr_status alloc_all(mr_ctx* c) {
   c->irr_cap = 1 << 16;
   A(c->irr_col, c->irr_cap);
   A(c->irr_w, c->irr_cap);
+  A(c->irr_wf, c->irr_cap);
   for (int q = 0; q < 6; q++) A(c->work[q], (int64_t)m * c->cap_leaves);
   A(c->red, (int64_t)152 * 16 * kMaxM);
   A(c->red_out, 64);
@@ -115,7 +116,7 @@ void free_all(mr_ctx* c) {
   cudaFree(c->V); cudaFree(c->Vnew); cudaFree(c->fl_state); cudaFree(c->fl_forced);
   cudaFree(c->fl_final); cudaFree(c->grank); cudaFree(c->tag); cudaFree(c->scan_tmp);
   cudaFree(c->itmp); cudaFree(c->nbr); cudaFree(c->leaf_lvl); cudaFree(c->irr_leaf); cudaFree(c->reg_tab);
-  cudaFree(c->irr_cnt); cudaFree(c->irr_ptr); cudaFree(c->irr_col); cudaFree(c->irr_w);
+  cudaFree(c->irr_cnt); cudaFree(c->irr_ptr); cudaFree(c->irr_col); cudaFree(c->irr_w); cudaFree(c->irr_wf);
   for (int q = 0; q < 6; q++) cudaFree(c->work[q]);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->complexity); cudaFree(c->dc);
   cudaFree(c->rho_bits);

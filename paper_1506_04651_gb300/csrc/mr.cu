@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
                const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
                const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf, Level L, int slot,
                int32_t* __restrict__ cnt, int32_t* __restrict__ col, double* __restrict__ wout,
-               unsigned long long* rho_bits, DevCounters* dc) {
+               float* __restrict__ wout_f, unsigned long long* rho_bits, DevCounters* dc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kC = IrrCfg<D>::kCells, kS = IrrCfg<D>::kSort;
   IrrShared<D>& S = reinterpret_cast<IrrShared<D>*>(smem_raw)[threadIdx.x >> 5];
@@ -704,6 +704,7 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
       if (ok) {
         col[row * (int64_t)slot + rank] = kq;
         wout[row * (int64_t)slot + rank] = S.sval[q];
+        wout_f[row * (int64_t)slot + rank] = (float)S.sval[q];
       }
     }
     for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
@@ -989,11 +990,14 @@ mr_status build_tables(mr_ctx* c) {
     if (need > c->irr_cap) {
       cudaFree(c->irr_col);
       cudaFree(c->irr_w);
+      cudaFree(c->irr_wf);
       c->irr_col = nullptr;
       c->irr_w = nullptr;
+      c->irr_wf = nullptr;
       c->irr_cap = need + need / 2 + 1024;
       MR_CUDA(c, cudaMalloc(&c->irr_col, sizeof(int32_t) * c->irr_cap));
       MR_CUDA(c, cudaMalloc(&c->irr_w, sizeof(double) * c->irr_cap));
+      MR_CUDA(c, cudaMalloc(&c->irr_wf, sizeof(float) * c->irr_cap));
     }
     int nsm = 152, dev = 0;
     cudaGetDevice(&dev);
@@ -1004,14 +1008,14 @@ mr_status build_tables(mr_ctx* c) {
       int grid = (int)std::min<int64_t>((nrows + IrrCfg<2>::kWarps - 1) / IrrCfg<2>::kWarps, (int64_t)nsm * 16);
       k_irr_rows<2><<<grid, 32 * IrrCfg<2>::kWarps, sm, c->stream>>>(
           c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, slot, c->irr_cnt, c->irr_col,
-          c->irr_w, c->rho_bits, c->dc);
+          c->irr_w, c->irr_wf, c->rho_bits, c->dc);
     } else {
       const size_t sm = sizeof(IrrShared<3>) * IrrCfg<3>::kWarps;
       MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       int grid = (int)std::min<int64_t>((nrows + IrrCfg<3>::kWarps - 1) / IrrCfg<3>::kWarps, (int64_t)nsm * 16);
       k_irr_rows<3><<<grid, 32 * IrrCfg<3>::kWarps, sm, c->stream>>>(
           c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, slot, c->irr_cnt, c->irr_col,
-          c->irr_w, c->rho_bits, c->dc);
+          c->irr_w, c->irr_wf, c->rho_bits, c->dc);
     }
     c->launches++;
     MR_CUDA(c, cudaGetLastError());

@@ -153,6 +153,7 @@ struct mr_ctx {
   int64_t* irr_ptr = nullptr;        // [cap_leaves + 1]
   int32_t* irr_col = nullptr;
   double* irr_w = nullptr;
+  float* irr_wf = nullptr;           // the merged-row weights in FP32 (exact, dyadic)
   int64_t irr_cap = 0;
   int irr_slot = 0;                  // row stride of irr_col / irr_w
   double* rock_tab = nullptr;        // ROCK4-type coefficients of every stage count

@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "mr_internal.cuh"
@@ -52,11 +53,13 @@ struct StageArgs {
 };
 
 __constant__ double c_ih2[kMaxL + 1];
+__constant__ float c_ih2f[kMaxL + 1];
 
 struct IrrRows {
   const int32_t* cnt;
   const int32_t* col;
   const double* w;
+  const float* wf;  // the same weights in FP32 (exact: dyadic), for the mixed form
   int slot;
 };
 
@@ -227,14 +230,18 @@ __device__ void rock_prepare(const PersArgs& P, RockCtl& C, int64_t N, double le
 enum { K_STAGE = 0, K_H3, K_H2, K_H1, K_H0, K_FSAL, K_STAGE1 };
 constexpr int kPhaseFinish = 1000;  // phases 2..n: stages; kPhaseFinish + K_*: the other sweeps
 
+// VT: arithmetic of the stage vectors (double, or float in the mixed form);
+// the error norm is accumulated in double either way
+template <typename VT>
 struct Ops {
-  const double *x, *a, *b, *yn;
-  double *out, *acc, *lx;
-  double ca, cb, cl, e0, e1, e2;
+  const VT *x, *a, *b, *yn;
+  VT *out, *acc, *lx;
+  VT ca, cb, cl, e0, e1, e2;
   int kind;
 };
 
-__device__ inline void combine(const Ops& o, int64_t r, double Lx, double tol, double& err) {
+template <typename VT>
+__device__ inline void combine(const Ops<VT>& o, int64_t r, VT Lx, double tol, double& err) {
   switch (o.kind) {
     case K_STAGE:
       o.out[r] = o.ca * o.a[r] + o.cb * o.b[r] + o.cl * Lx;
@@ -248,30 +255,31 @@ __device__ inline void combine(const Ops& o, int64_t r, double Lx, double tol, d
       o.out[r] = o.ca * o.a[r] + o.cl * Lx;
       break;
     case K_H1: {
-      const double v = o.ca * o.a[r] + o.cl * Lx;  // h1 = w1 yP + z h2
+      const VT v = o.ca * o.a[r] + o.cl * Lx;  // h1 = w1 yP + z h2
       o.out[r] = v;
       o.acc[r] = o.e0 * o.a[r] + o.e1 * v + o.e2 * o.x[r];
       break;
     }
     case K_H0: {
-      const double v = o.a[r] + o.cl * Lx;  // y_{n+1} = yP + z h1
+      const VT v = o.a[r] + o.cl * Lx;  // y_{n+1} = yP + z h1
       o.out[r] = v;
       o.acc[r] += v;
       break;
     }
     default: {  // embedded estimate e = acc + d z y_{n+1}; L y_{n+1} is kept
       o.lx[r] = Lx;
-      const double ee = o.acc[r] + o.cl * Lx;
-      const double sc = tol + tol * fmax(fabs(o.yn[r]), fabs(o.x[r]));
+      const double ee = (double)(o.acc[r] + o.cl * Lx);
+      const double sc = tol + tol * fmax(fabs((double)o.yn[r]), fabs((double)o.x[r]));
       err += (ee / sc) * (ee / sc);
     }
   }
 }
 
-template <int D, int M>
-__global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersArgs P, const int4* __restrict__ reg, int64_t nreg,
-                                                            IrrRows R, const int32_t* __restrict__ irr_leaf,
-                                                            int64_t nirr) {
+template <int D, int M, typename VT>
+__global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
+    k_rock_persistent(PersArgs P, const int4* __restrict__ reg, int64_t nreg, IrrRows R,
+                      const int32_t* __restrict__ irr_leaf, int64_t nirr) {
+  constexpr bool kF64 = std::is_same<VT, double>::value;
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[kBlock];
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
   __shared__ int s_pr[kMaxM][3];  // pool indices of the three recurrence buffers
   __shared__ int s_ly[kMaxM];   // which of W4 / W5 holds L y of the state
   __shared__ double s_err2[kMaxM];
-  __shared__ Ops s_ops[M];
+  __shared__ Ops<VT> s_ops[M];
   __shared__ int s_act[M];
   const int64_t N = P.N, capL = P.capL;
   if (threadIdx.x == 0) {
@@ -296,14 +304,32 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   const double leafb = N * (8.0 * D + 1.0);
-  auto pool = [&](int i, int k) { return (k == 0 ? P.U : P.W[k - 1]) + (int64_t)i * capL; };
-  auto Wp = [&](int q, int i) { return P.W[q] + (int64_t)i * capL; };
+  // vector q of species i: FP64: the state U (pool 0), W0..W2 (pool 1..3),
+  // W3 (error accumulator), W4, W5 (L y); FP32: twelve float vectors carved
+  // from the six work buffers, pool 0..3 = vectors 0..3 (vector 0 holds a
+  // float copy of the state), accumulator 4, L y 5 and 6
+  auto fvec = [&](int q, int i) -> VT* {
+    return reinterpret_cast<VT*>(reinterpret_cast<float*>(P.W[q >> 1]) + (q & 1) * (int64_t)P.m * capL) +
+           (int64_t)i * capL;
+  };
+  auto pool = [&](int i, int k) -> VT* {
+    if constexpr (kF64)
+      return reinterpret_cast<VT*>(k == 0 ? P.U : P.W[k - 1]) + (int64_t)i * capL;
+    else
+      return fvec(k, i);
+  };
+  auto Wp = [&](int q, int i) -> VT* {  // q = 3 accumulator, 4 / 5 L y
+    if constexpr (kF64)
+      return reinterpret_cast<VT*>(P.W[q]) + (int64_t)i * capL;
+    else
+      return fvec(q + 1, i);
+  };
   auto Y = [&](int i) { return pool(i, s_py[i]); };
   auto Rb = [&](int i, int q) { return pool(i, s_pr[i][q]); };
   auto LY = [&](int i) { return Wp(4 + s_ly[i], i); };
   auto LC = [&](int i) { return Wp(5 - s_ly[i], i); };
   // operands of species i in `phase`; false if the species sits it out
-  auto ops_for = [&](int phase, int i, Ops& o) -> bool {
+  auto ops_for = [&](int phase, int i, Ops<VT>& o) -> bool {
     if (C.done[i]) return false;
     const double* tb = P.tab.data + P.tab.off[C.s[i]];
     const double hd = C.h[i] * P.Dc[i];
@@ -320,9 +346,9 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
       o.a = o.x;
       o.b = j == 2 ? Y(i) : Rb(i, (j - 3) % 3);
       o.out = Rb(i, (j - 1) % 3);
-      o.ca = tb[10 + (j - 1)];
-      o.cb = tb[10 + n + (j - 1)];
-      o.cl = tb[10 + 2 * n + (j - 1)] * hd;
+      o.ca = (VT)tb[10 + (j - 1)];
+      o.cb = (VT)tb[10 + n + (j - 1)];
+      o.cl = (VT)(tb[10 + 2 * n + (j - 1)] * hd);
       return true;
     }
     const double* w = tb + 1;
@@ -332,17 +358,17 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
     switch (o.kind) {
       case K_STAGE1:
         o.x = Y(i); o.a = Y(i); o.out = Rb(i, 0); o.lx = LY(i);
-        o.ca = tb[10]; o.cl = tb[10 + 2 * n] * hd;
+        o.ca = (VT)tb[10]; o.cl = (VT)(tb[10 + 2 * n] * hd);
         break;
-      case K_H3: o.x = Rb(i, a); o.a = Rb(i, a); o.out = Rb(i, b); o.ca = w[3]; o.cl = w[4] * hd; break;
-      case K_H2: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.ca = w[2]; o.cl = hd; break;
+      case K_H3: o.x = Rb(i, a); o.a = Rb(i, a); o.out = Rb(i, b); o.ca = (VT)w[3]; o.cl = (VT)(w[4] * hd); break;
+      case K_H2: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.ca = (VT)w[2]; o.cl = (VT)hd; break;
       case K_H1:
-        o.x = Rb(i, cc); o.a = Rb(i, a); o.out = Rb(i, b); o.acc = Wp(3, i); o.ca = w[1]; o.cl = hd;
-        o.e0 = e[0]; o.e1 = e[1]; o.e2 = e[2];
+        o.x = Rb(i, cc); o.a = Rb(i, a); o.out = Rb(i, b); o.acc = Wp(3, i); o.ca = (VT)w[1]; o.cl = (VT)hd;
+        o.e0 = (VT)e[0]; o.e1 = (VT)e[1]; o.e2 = (VT)e[2];
         break;
-      case K_H0: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.acc = Wp(3, i); o.ca = 1.0; o.cl = hd; break;
+      case K_H0: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.acc = Wp(3, i); o.ca = (VT)1; o.cl = (VT)hd; break;
       default:
-        o.x = Rb(i, cc); o.a = nullptr; o.out = nullptr; o.acc = Wp(3, i); o.lx = LC(i); o.cl = e[3] * hd;
+        o.x = Rb(i, cc); o.a = nullptr; o.out = nullptr; o.acc = Wp(3, i); o.lx = LC(i); o.cl = (VT)(e[3] * hd);
     }
     return true;
   };
@@ -358,21 +384,25 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
   constexpr int MG = (M + G - 1) / G;  // species a merged-row lane finishes
   const int sub = lane & (G - 1);
   auto sweep = [&](double* err, double* err_row) {
-    const Ops* o = s_ops;
+    const Ops<VT>* o = s_ops;
     const int* act = s_act;
     for (int64_t q = tid; q < nreg; q += nth) {
       const int4 e0 = reg[2 * q], e1 = reg[2 * q + 1];
       const int v[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
       const int64_t r = v[0];
-      const double ih2 = c_ih2[v[1 + 2 * D]];
+      VT ih2;
+      if constexpr (kF64)
+        ih2 = c_ih2[v[1 + 2 * D]];
+      else
+        ih2 = c_ih2f[v[1 + 2 * D]];
 #pragma unroll
       for (int i = 0; i < M; i++) {
         if (!act[i]) continue;
-        const double* x = o[i].x;
-        double sx = x[v[1]];
+        const VT* x = o[i].x;
+        VT sx = x[v[1]];
 #pragma unroll
         for (int f = 1; f < 2 * D; f++) sx += x[v[1 + f]];
-        combine(o[i], r, (sx - 2.0 * D * x[r]) * ih2, P.tol, err[i]);
+        combine<VT>(o[i], r, (sx - (VT)(2 * D) * x[r]) * ih2, P.tol, err[i]);
       }
     }
     const int64_t grp = tid / G, ngrp = nth / G;
@@ -380,19 +410,23 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
     for (int64_t k = 0; k < rounds; k++) {
       const int64_t row = grp + k * ngrp;
       const bool have = row < nirr;
-      double v[M];
+      VT v[M];
 #pragma unroll
-      for (int i = 0; i < M; i++) v[i] = 0.0;
+      for (int i = 0; i < M; i++) v[i] = (VT)0;
       int32_t r = 0;
       if (have) {
         r = irr_leaf[row];
         const int cnt = R.cnt[row];
         const int32_t* col = R.col + row * (int64_t)R.slot;
-        const double* wr = R.w + row * (int64_t)R.slot;
+        const VT* wr;
+        if constexpr (kF64)
+          wr = R.w + row * (int64_t)R.slot;
+        else
+          wr = R.wf + row * (int64_t)R.slot;
 #pragma unroll 4
         for (int e = sub; e < cnt; e += G) {
           const int32_t cidx = col[e];
-          const double we = wr[e];
+          const VT we = wr[e];
 #pragma unroll
           for (int i = 0; i < M; i++)
             if (act[i]) v[i] += we * o[i].x[cidx];
@@ -407,11 +441,11 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
 #pragma unroll
         for (int i0 = 0; i0 < M; i0 += G) {
           const int i = i0 + sub;
-          double vi = v[i0];
+          VT vi = v[i0];
 #pragma unroll
           for (int u = 1; u < G; u++)
             if (i0 + u < M && sub == u) vi = v[i0 + u];
-          if (i < M && act[i]) combine(o[i], r, vi, P.tol, err_row[i0 / G]);
+          if (i < M && act[i]) combine<VT>(o[i], r, vi, P.tol, err_row[i0 / G]);
         }
       }
     }
@@ -419,6 +453,15 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
   __syncthreads();
   if (threadIdx.x == 0) rock_prepare(P, C, N, leafb);
   __syncthreads();
+  if constexpr (!kF64) {
+    // the mixed form integrates a float copy of the state
+    for (int i = 0; i < P.m; i++) {
+      const double* u = P.U + (int64_t)i * capL;
+      VT* y = pool(i, 0);
+      for (int64_t r = tid; r < N; r += nth) y[r] = (VT)u[r];
+    }
+    grid.sync();
+  }
   bool first = true;
   for (int round = 0; round < 20000; round++) {
     if (C.finished) break;
@@ -436,9 +479,9 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
       for (int i = 0; i < M; i++) {
         if (C.done[i]) continue;
         const double* tb = P.tab.data + P.tab.off[C.s[i]];
-        const double ca = tb[10], cl = tb[10 + 2 * C.n[i]] * C.h[i] * P.Dc[i];
-        const double *y = Y(i), *ly = LY(i);
-        double* out = Rb(i, 0);
+        const VT ca = (VT)tb[10], cl = (VT)(tb[10 + 2 * C.n[i]] * C.h[i] * P.Dc[i]);
+        const VT *y = Y(i), *ly = LY(i);
+        VT* out = Rb(i, 0);
         for (int64_t r = tid; r < N; r += nth) out[r] = ca * y[r] + cl * ly[r];
       }
     }
@@ -520,12 +563,13 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2) k_rock_persistent(PersA
     __syncthreads();
   }
   if (threadIdx.x == 0 && !C.finished) C.status = MR_EROCK_STEP;
-  // the final state back into the state array where a swap moved it
-  for (int i = 0; i < M; i++) {
-    if (s_py[i] == 0) continue;
-    const double* y = Y(i);
+  // the final state back into the state array where a swap moved it (FP64),
+  // or converted back (FP32)
+  for (int i = 0; i < P.m; i++) {
+    if (kF64 && s_py[i] == 0) continue;
+    const VT* y = Y(i);
     double* u = P.U + (int64_t)i * capL;
-    for (int64_t r = tid; r < N; r += nth) u[r] = y[r];
+    for (int64_t r = tid; r < N; r += nth) u[r] = (double)y[r];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.ctl = C;
 }
@@ -722,15 +766,20 @@ static mr_status init_ih2(mr_ctx* c) {
   std::lock_guard<std::mutex> lock(g_ih2_mu);
   if (dev >= 0 && dev < 256 && g_ih2_done[dev]) return MR_OK;
   double ih2[kMaxL + 1];
-  for (int j = 0; j <= kMaxL; j++) ih2[j] = ldexp(1.0, 2 * j);
+  float ih2f[kMaxL + 1];
+  for (int j = 0; j <= kMaxL; j++) {
+    ih2[j] = ldexp(1.0, 2 * j);
+    ih2f[j] = ldexpf(1.0f, 2 * j);
+  }
   MR_CUDA(c, cudaMemcpyToSymbol(c_ih2, ih2, sizeof ih2));
+  MR_CUDA(c, cudaMemcpyToSymbol(c_ih2f, ih2f, sizeof ih2f));
   if (dev >= 0 && dev < 256) g_ih2_done[dev] = true;
   return MR_OK;
 }
 
 static void launch_rock(mr_ctx* c, const StageArgs& A, int64_t N, int nb, int* nev = nullptr) {
   if (nev && *nev < 256) cudaEventRecord(c->tev[2 * *nev], c->stream);
-  IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_slot};
+  IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_wf, c->irr_slot};
   if (c->d == 2)
     k_rock<2><<<nb, kBlock, 0, c->stream>>>(A, N, c->cap_leaves, c->nbr, c->leaf_lvl, R, c->red);
   else
@@ -828,11 +877,23 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   // kernels for 1, 3 and up to 16 species (unused species of the 16-wide
   // kernel are marked done)
   const int M = m == 1 ? 1 : (m == 3 ? 3 : 16);
-  const void* kern =
-      c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1>
-                          : (M == 3 ? (const void*)k_rock_persistent<2, 3> : (const void*)k_rock_persistent<2, 16>))
-                : (M == 1 ? (const void*)k_rock_persistent<3, 1>
-                          : (M == 3 ? (const void*)k_rock_persistent<3, 3> : (const void*)k_rock_persistent<3, 16>));
+  // FP64 stage vectors, or FP32 in the mixed form
+  const bool f32 = c->prob.precision == MR_MIXED;
+  const void* kern;
+  if (!f32)
+    kern = c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1, double>
+                               : (M == 3 ? (const void*)k_rock_persistent<2, 3, double>
+                                         : (const void*)k_rock_persistent<2, 16, double>))
+                     : (M == 1 ? (const void*)k_rock_persistent<3, 1, double>
+                               : (M == 3 ? (const void*)k_rock_persistent<3, 3, double>
+                                         : (const void*)k_rock_persistent<3, 16, double>));
+  else
+    kern = c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1, float>
+                               : (M == 3 ? (const void*)k_rock_persistent<2, 3, float>
+                                         : (const void*)k_rock_persistent<2, 16, float>))
+                     : (M == 1 ? (const void*)k_rock_persistent<3, 1, float>
+                               : (M == 3 ? (const void*)k_rock_persistent<3, 3, float>
+                                         : (const void*)k_rock_persistent<3, 16, float>));
   MR_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return MR_ECUDA;
   // enough blocks to cover the leaves, at most what is co-resident
@@ -860,7 +921,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   for (int q = 0; q < 6; q++) P.W[q] = c->work[q];
   P.part = c->red;
   P.ctl = dctl;
-  IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_slot};
+  IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_wf, c->irr_slot};
   const int4* reg = c->reg_tab;
   const int32_t* irr_leaf = c->irr_leaf;
   int64_t nirr = c->stats.irregular_rows;
