@@ -568,6 +568,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCH))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--J", type=int, default=0,
+                    help="run the workload at another finest level (profiling captures of a smaller case); "
+                         "the line's config records it")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -578,6 +581,9 @@ def main():
         run_batch(args, BATCH[args.workload])
         return
     w = WORKLOADS[args.workload]
+    if args.J and args.J != w["J"]:
+        w = dict(w, J=args.J, oracle_J=min(w.get("oracle_J", args.J), args.J),
+                 desc=w["desc"] + f" -- run at finest level J={args.J}")
     if args.impl == "reference":
         run_reference(args, w)
     else:
