@@ -57,8 +57,9 @@ WORKLOADS = {
 BATCH = {"batch64_bz2d": dict(n=64, dt=1e-3,
                               desc="64 independent 2D BZ instances, seeded J ~ U{7..10}, f ~ U[0.9, 2.0], "
                                    "eta log-uniform in [1e-4, 1e-2], front position ~ U[0.2, 0.8] "
-                                   "(master seed 2026); one context and CUDA stream per instance, "
-                                   "driven concurrently by host threads; FP64")}
+                                   "(master seed 2026); native batch: adaptation and diffusion of every "
+                                   "instance on its own stream, reaction half steps as joint Radau5 launches "
+                                   "over all instances' leaves; FP64")}
 DEFAULT = "bz2d_J10_eta1e-3"
 TOL = 1e-6
 
@@ -476,12 +477,10 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
 
 
 def run_batch(args, b):
-    """Batched serving workload: every instance steps on its own stream; the GPU
-    overlaps their kernels.  value = leaves of all instances and steps / the
-    device makespan (start event on the default stream, which every instance
-    stream waits on, to the latest end event)."""
-    import concurrent.futures as cf
-
+    """Batched serving workload through the native batch (mr_batch_*): every
+    instance adapts and diffuses on its own stream, the reaction half steps of
+    all instances are joint Radau5 launches.  value = leaves of all instances
+    and steps / the run's device time (CUDA events around mr_batch_run)."""
     import torch
     import __graft_entry__ as g
     g.build()
@@ -492,69 +491,118 @@ def run_batch(args, b):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     insts = I.batch_instances(b["n"])
-    streams = [torch.cuda.Stream(device=dev) for _ in insts]
-    ctxs = []
-    for inst, st in zip(insts, streams):
-        p = mr.problem(2, inst["J"], params=(1e-2, 1e-5, inst["f"], 2e-3))
-        c = mr.Context(p, stream=st)
-        u0 = I.bz_front_smooth_2d(inst["J"], inst["seed"] & 0xFFFFFFFF, x0=inst["x0"], f=inst["f"])
-        c.build(torch.from_numpy(u0).to(dev), inst["eta"])
-        ctxs.append(c)
-    torch.cuda.synchronize()
-    pool = cf.ThreadPoolExecutor(max_workers=min(len(ctxs), 32))
+    eta = [inst["eta"] for inst in insts]
+    u0s = [I.bz_front_smooth_2d(inst["J"], inst["seed"] & 0xFFFFFFFF, x0=inst["x0"], f=inst["f"]) for inst in insts]
 
-    def run(i, k):
-        n = 0
-        for _ in range(k):
-            ctxs[i].strang(b["dt"], insts[i]["eta"], TOL, TOL, TOL)
-            n += ctxs[i].stats()["leaves"]
-        return n
+    def make(prec):
+        B = mr.Batch([mr.problem(2, inst["J"], params=(1e-2, 1e-5, inst["f"], 2e-3), precision=prec)
+                      for inst in insts])
+        for k, inst in enumerate(insts):
+            B[k].build(torch.from_numpy(u0s[k]).to(dev), inst["eta"])
+        return B
 
-    list(pool.map(lambda i: run(i, args.warmup), range(len(ctxs))))
-    torch.cuda.synchronize()
-    st0 = [c.stats() for c in ctxs]
-    start = torch.cuda.Event(enable_timing=True)
-    ends = [torch.cuda.Event(enable_timing=True) for _ in ctxs]
+    B = make(mr.MR_FP64)
+    B.run(args.warmup, b["dt"], eta, TOL, TOL, TOL)
+    start = [B[k].leaves() for k in range(B.n)]  # the timed steps' starting state, for the e2e replay
+    launches0 = sum(B[k].stats()["kernel_launches"] for k in range(B.n))
     clocks = ClockSampler(local)
     clocks.start()
-    start.record(torch.cuda.current_stream())
-    for st in streams:
-        st.wait_event(start)
-
-    def timed(i):
-        n = run(i, args.steps)
-        ends[i].record(streams[i])
-        return n
-
-    leaves = sum(pool.map(timed, range(len(ctxs))))
+    torch.cuda.synchronize()
+    B.run(args.steps, b["dt"], eta, TOL, TOL, TOL)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = max(start.elapsed_time(e) for e in ends)
-    st1 = [c.stats() for c in ctxs]
-    launches = sum(b1["kernel_launches"] - a["kernel_launches"] for a, b1 in zip(st0, st1))
-    rad_ms = sum(b1["radau_kernel_ms"] - a["radau_kernel_ms"] for a, b1 in zip(st0, st1))
-    rad_fl = sum(b1["radau_alg_flops"] - a["radau_alg_flops"] for a, b1 in zip(st0, st1))
+    st = B.stats()
+    launches = sum(B[k].stats()["kernel_launches"] for k in range(B.n)) - launches0 + st["react_launches"]
+    ms = st["ms_device"]
+    value = st["leaf_updates"] / (ms * 1e-3)
     fp64_tf, _ = mr.fp64_fma_rate()
-    # Radau5 kernels of different instances overlap, so the achieved FP64 rate
-    # of the batch is its algorithmic FP64 work over the makespan
-    ach = rad_fl / (ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "k_radau (Radau5, FP64), all instances", "achieved": ach,
+    ach = st["radau_alg_flops"] / (st["ms_react_kernel"] * 1e-3) / 1e12 if st["ms_react_kernel"] else 0.0
+    roof = {"bound": "alu", "kernel": "k_radau (joint Radau5 launch over all instances, FP64)", "achieved": ach,
             "peak": fp64_tf, "unit": "TFLOP/s", "frac": ach / fp64_tf, "traffic": None,
-            "peak_source": "measured FP64 FMA rate of this GPU (library probe)",
-            "note": "algorithmic FP64 work of all Radau5 launches / batch makespan",
-            "radau_kernel_ms_summed_over_streams": rad_ms}
-    line = {"metric": METRIC, "value": leaves / (ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+            "peak_source": "measured FP64 FMA rate of this GPU (library probe, 2 flop/FMA)",
+            "launches": st["react_launches"], "ms_per_launch": st["ms_react_kernel"] / max(st["react_launches"], 1)}
+    final64 = [B[k].leaves() for k in range(B.n)]
+
+    # end to end: the timed steps replayed from the same starting state, every
+    # step every instance's state in from pinned host memory and out again
+    pinned = []
+    for k, (keys, vals) in enumerate(start):
+        cap = max(len(keys), max(len(f[0]) for f in [final64[k]])) * 2
+        bufs = [torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64),
+                torch.empty(3 * cap, dtype=torch.float64, pin_memory=True).numpy()]
+        n0 = len(keys)
+        bk, bv = bufs[0][:n0], bufs[1][:3 * n0].reshape(3, n0)
+        bk[:] = keys
+        bv[:] = vals
+        pinned.append((bufs, bk, bv))
+    n_e2e = min(args.steps, 5)
+    h2d = d2h = 0
+    e2e_leaves = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        for k in range(B.n):
+            _, bk, bv = pinned[k]
+            B[k].set_leaves(bk, bv)
+            h2d += bk.nbytes + bv.nbytes
+        B.run(1, b["dt"], eta, TOL, TOL, TOL)
+        e2e_leaves += B.stats()["leaf_updates"]
+        for k in range(B.n):
+            bufs, _, _ = pinned[k]
+            n = B[k].num_leaves()
+            if 3 * n > len(bufs[1]):
+                bufs[0] = torch.empty(2 * n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+                bufs[1] = torch.empty(6 * n, dtype=torch.float64, pin_memory=True).numpy()
+            bk, bv = B[k].leaves(bufs[0][:n], bufs[1][:3 * n].reshape(3, n))
+            d2h += bk.nbytes + bv.nbytes
+            pinned[k] = (bufs, bk, bv)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": e2e_leaves / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
+           "d2h_bytes_per_step": d2h // n_e2e, "steps": n_e2e,
+           "note": "the first timed steps replayed from the same starting state: every instance's "
+                   "mr_set_leaves(host), mr_batch_run(1 step), every instance's mr_get_leaves(host); wall clock"}
+    B.close()
+
+    # mixed form: the same batch and steps with FP32 Newton factorisations and ROCK4 stages
+    mixed = None
+    if not args.no_mixed:
+        Bm = make(mr.MR_MIXED)
+        Bm.run(args.warmup, b["dt"], eta, TOL, TOL, TOL)
+        Bm.run(args.steps, b["dt"], eta, TOL, TOL, TOL)
+        sm = Bm.stats()
+        num = den = 0.0
+        errs = []
+        for k in range(Bm.n):
+            km, vm = Bm[k].leaves()
+            kf, vf = final64[k]
+            if np.array_equal(km, kf):
+                vol = np.ldexp(1.0, (2 * (insts[k]["J"] - (kf >> np.uint64(48)).astype(np.int64))).astype(np.int32))
+                errs.append(max(float(np.sum(vol * np.abs(vm[i] - vf[i])) / np.sum(vol * np.abs(vf[i])))
+                                for i in range(3)))
+            else:
+                f64 = finest_grid(kf, vf, 2, insts[k]["J"])
+                mix = finest_grid(km, vm, 2, insts[k]["J"])
+                errs.append(max(float(np.sum(np.abs(mix[i] - f64[i])) / np.sum(np.abs(f64[i]))) for i in range(3)))
+        mvalue = sm["leaf_updates"] / (sm["ms_device"] * 1e-3)
+        mixed = {"value": mvalue, "ms_per_step": sm["ms_device"] / args.steps, "speedup_vs_fp64": mvalue / value,
+                 "rel_l1_vs_fp64_path_max_over_instances": max(errs),
+                 "form": "Radau5 Newton factorisations and solves in FP32; ROCK4 stage vectors in FP32; "
+                         "Radau5 residuals, both error norms, step control, the state between sub-steps, "
+                         "details and mass in FP64"}
+        Bm.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": b["desc"], "instances": len(ctxs),
-                       "J": [i["J"] for i in insts],
-                       "leaves_total_last_step": sum(s["leaves"] for s in st1),
+            "config": {"workload": args.workload, "desc": b["desc"], "instances": len(insts),
+                       "J": [i["J"] for i in insts], "host_threads": st["threads"],
+                       "leaves_total_last_step": sum(len(f[0]) for f in final64),
                        "l2": "inputs larger than L2 (all instances' state and work vectors)"},
-            "roofline": roof, "gpu_launches": launches, "clocks": clk}
-    pool.shutdown()
-    for c in ctxs:
-        c.close()
+            "roofline": roof, "e2e": e2e, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
+            "mixed": mixed, "kernels": {"joint_radau": {"ms": st["ms_react_kernel"], "launches": st["react_launches"],
+                                                       "tflops": ach}}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

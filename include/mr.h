@@ -167,6 +167,50 @@ mr_status diffuse_rock4(mr_ctx *ctx, double dt, double tol);
 mr_status strang_step(mr_ctx *ctx, double dt, double eta, double rtol, double atol,
                       double rock_tol);
 
+/*
+ * Batched serving: n independent instances (own grid depth, parameters and
+ * threshold each) stepped together on the current device.
+ *   mr_batch_create  n contexts (probs[i], each with its own CUDA stream) and
+ *                    a pool of `threads` host threads (<= 0: one per core, at
+ *                    most 32).  MR_EINVAL for n outside [1, 4096] or a bad
+ *                    problem (as mr_create).
+ *   mr_batch_context the i-th instance's context, for mr_build / mr_set_leaves
+ *                    / mr_get_leaves / mr_mass ... (owned by the batch; NULL
+ *                    for a bad index).  Do not destroy it.
+ *   mr_batch_run     nsteps Strang steps of every instance, eta[i] its
+ *                    threshold: the adaptation and the diffusion of all
+ *                    instances run concurrently on their streams, and each
+ *                    reaction half step of all instances is one persistent
+ *                    Radau5 launch over the union of their leaves (when all
+ *                    instances use the BZ or all the NAGUMO model with one
+ *                    precision; otherwise one launch per instance).  Every
+ *                    cell is integrated with the same arithmetic as by
+ *                    strang_step, so results equal stepping each context
+ *                    alone.  Synchronises before returning; the first error
+ *                    wins (per-instance detail in each context's last error).
+ *   mr_batch_get_stats counters of the last mr_batch_run.  In the joint form
+ *                    the Radau5 counters are batch totals (the contexts' own
+ *                    Radau5 counters are not updated).
+ */
+typedef struct mr_batch mr_batch;
+typedef struct {
+  int64_t instances, threads, steps;
+  int64_t leaf_updates;        /* sum over steps and instances of the leaves after adaptation */
+  double ms_device;            /* device time of the run: start event to end event */
+  double ms_react_kernel;      /* summed device time of the joint Radau5 launches */
+  int64_t react_launches;      /* joint Radau5 launches */
+  int64_t radau_fev, radau_jac, radau_steps, radau_accept, radau_reject, radau_newton, radau_dec;
+  double radau_alg_flops;      /* algorithmic FP64 operations of the joint launches */
+  int32_t joint_reaction, reserved;
+} mr_batch_stats;
+
+mr_status mr_batch_create(int n, const mr_problem *probs, int threads, mr_batch **out);
+mr_ctx *mr_batch_context(mr_batch *b, int i);
+mr_status mr_batch_run(mr_batch *b, int nsteps, double dt, const double *eta, double rtol, double atol,
+                       double rock_tol);
+mr_status mr_batch_get_stats(const mr_batch *b, mr_batch_stats *out);
+void mr_batch_destroy(mr_batch *b);
+
 /* Checkpoint and resume.  mr_save writes the current leaves to `path`:
  * a 64-byte header (8-byte magic "MRGB300\0"; int32 format version 1, dim,
  * J, jmin, m, model, precision, 0; int64 leaf count; 16 zero bytes), the model parameters

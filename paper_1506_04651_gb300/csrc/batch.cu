@@ -1,0 +1,279 @@
+// Batched serving: many independent instances (each its own grid, depth,
+// parameters and threshold) stepped together on one GPU.  Every instance
+// keeps its own context and CUDA stream; the grid adaptation and the
+// diffusion sub-step of all instances run concurrently, driven by a pool of
+// host threads (their phases synchronise with the host to size the trees),
+// and the two reaction sub-steps of every Strang step run as one persistent
+// Radau5 launch over the union of all instances' leaves, so that the stiff
+// cells of one instance overlap the cells at rest of the others and the
+// launch has one tail instead of one per instance.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "mr_internal.cuh"
+
+namespace mrg {
+namespace {
+
+// fixed pool of host threads running f(0 .. n-1) on demand
+class Pool {
+ public:
+  Pool(int nthreads, int dev) : dev_(dev) {
+    for (int q = 0; q < nthreads; q++) th_.emplace_back([this] { worker(); });
+  }
+  ~Pool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  void run(int n, const std::function<void(int)>& f) {
+    std::unique_lock<std::mutex> lk(mu_);
+    f_ = &f;
+    n_ = n;
+    next_ = 0;
+    busy_ = (int)th_.size();
+    gen_++;
+    cv_.notify_all();
+    done_.wait(lk, [this] { return busy_ == 0; });
+    f_ = nullptr;
+  }
+
+ private:
+  void worker() {
+    cudaSetDevice(dev_);
+    int seen = 0;
+    for (;;) {
+      const std::function<void(int)>* f;
+      int n;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        f = f_;
+        n = n_;
+      }
+      for (int i = next_++; i < n; i = next_++) (*f)(i);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--busy_ == 0) done_.notify_all();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* f_ = nullptr;
+  int n_ = 0, gen_ = 0, busy_ = 0;
+  std::atomic<int> next_{0};
+  bool stop_ = false;
+  int dev_;
+};
+
+}  // namespace
+}  // namespace mrg
+
+struct mr_batch {
+  int n = 0, dev = 0;
+  std::vector<mr_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev;  // one per instance
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_joint = nullptr;
+  mrg::Pool* pool = nullptr;
+  mrg::BatchReactScratch scratch;
+  mr_batch_stats stats;
+  const char* last_error = "";
+};
+
+using namespace mrg;
+
+namespace {
+
+void batch_free(mr_batch* b) {
+  delete b->pool;
+  for (mr_ctx* c : b->ctx)
+    if (c) mr_destroy(c);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
+  if (b->ev_end) cudaEventDestroy(b->ev_end);
+  if (b->ev_joint) cudaEventDestroy(b->ev_joint);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  free_batch_scratch(b->scratch);
+  delete b;
+}
+
+// run f on every instance with the pool; the first error wins
+mr_status for_all(mr_batch* b, const std::function<mr_status(int)>& f) {
+  std::atomic<int> first{0};
+  std::function<void(int)> g = [&](int i) {
+    const mr_status s = f(i);
+    if (s) {
+      int z = 0;
+      first.compare_exchange_strong(z, (int)s);
+    }
+  };
+  b->pool->run(b->n, g);
+  return (mr_status)first.load();
+}
+
+// both reaction half steps: one joint launch when every instance uses a
+// one-thread-per-cell model with the same precision, else per instance
+mr_status react_all(mr_batch* b, double dt, double rtol, double atol) {
+  bool joint = true;
+  for (mr_ctx* c : b->ctx)
+    joint = joint && (c->prob.model == MR_MODEL_BZ || c->prob.model == MR_MODEL_NAGUMO) &&
+            c->prob.model == b->ctx[0]->prob.model && c->prob.precision == b->ctx[0]->prob.precision;
+  if (!joint) {
+    b->stats.joint_reaction = 0;
+    return for_all(b, [&](int i) { return react(b->ctx[i], dt, rtol, atol); });
+  }
+  // the joint launch follows every instance's queued work and precedes its next
+  for (int i = 0; i < b->n; i++) {
+    if (cudaEventRecord(b->ev[i], b->streams[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ev[i], 0) != cudaSuccess)
+      return MR_ECUDA;
+  }
+  double ms = 0.0;
+  unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+  const mr_status s = react_batch(b->ctx.data(), b->n, dt, rtol, atol, b->stream, b->scratch, &ms, cnt);
+  if (s) return s;
+  if (cudaEventRecord(b->ev_joint, b->stream) != cudaSuccess) return MR_ECUDA;
+  for (int i = 0; i < b->n; i++)
+    if (cudaStreamWaitEvent(b->streams[i], b->ev_joint, 0) != cudaSuccess) return MR_ECUDA;
+  mr_batch_stats& S = b->stats;
+  S.joint_reaction = 1;
+  S.ms_react_kernel += ms;
+  S.react_launches++;
+  S.radau_fev += cnt[0];
+  S.radau_jac += cnt[1];
+  S.radau_steps += cnt[2];
+  S.radau_accept += cnt[3];
+  S.radau_reject += cnt[4];
+  S.radau_newton += cnt[5];
+  S.radau_dec += cnt[6];
+  // algorithmic FP64 operations per counted event (as for one context)
+  const bool bz = b->ctx[0]->prob.model == MR_MODEL_BZ;
+  S.radau_alg_flops += (bz ? 13 : 4) * (double)cnt[0] + (bz ? 10 : 4) * (double)cnt[1] +
+                       (bz ? 114 : 6) * (double)cnt[6] + (bz ? 271 : 30) * (double)cnt[5] +
+                       (bz ? 246 : 40) * (double)cnt[2];
+  return MR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mr_status mr_batch_create(int n, const mr_problem* probs, int threads, mr_batch** out) {
+  if (!out || !probs || n < 1 || n > 4096) return MR_EINVAL;
+  *out = nullptr;
+  mr_batch* b = new (std::nothrow) mr_batch();
+  if (!b) return MR_ENOMEM;
+  memset(&b->stats, 0, sizeof b->stats);
+  b->n = n;
+  cudaGetDevice(&b->dev);
+  b->ctx.assign(n, nullptr);
+  b->streams.assign(n, nullptr);
+  b->ev.assign(n, nullptr);
+  mr_status s = MR_OK;
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&b->ev_start) != cudaSuccess || cudaEventCreate(&b->ev_end) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_joint, cudaEventDisableTiming) != cudaSuccess)
+    s = MR_ECUDA;
+  for (int i = 0; i < n && !s; i++) {
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      s = MR_ECUDA;
+      break;
+    }
+    s = mr_create(&probs[i], b->streams[i], &b->ctx[i]);
+  }
+  if (s) {
+    batch_free(b);
+    return s;
+  }
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::max(1, std::min(n, threads > 0 ? threads : std::min(hw, 32)));
+  b->pool = new (std::nothrow) Pool(nt, b->dev);
+  if (!b->pool) {
+    batch_free(b);
+    return MR_ENOMEM;
+  }
+  b->stats.instances = n;
+  b->stats.threads = nt;
+  *out = b;
+  return MR_OK;
+}
+
+mr_ctx* mr_batch_context(mr_batch* b, int i) { return (b && i >= 0 && i < b->n) ? b->ctx[i] : nullptr; }
+
+mr_status mr_batch_run(mr_batch* b, int nsteps, double dt, const double* eta, double rtol, double atol,
+                       double rock_tol) {
+  if (!b || nsteps < 0 || !eta || !(dt > 0.0) || !(rtol > 0.0) || !(atol > 0.0) || !(rock_tol > 0.0))
+    return MR_EINVAL;
+  for (int i = 0; i < b->n; i++)
+    if (!(eta[i] >= 0.0) || !isfinite(eta[i])) return MR_EINVAL;
+  mr_batch_stats& S = b->stats;
+  S.steps = 0;
+  S.leaf_updates = 0;
+  S.ms_react_kernel = 0.0;
+  S.react_launches = 0;
+  S.radau_fev = S.radau_jac = S.radau_steps = S.radau_accept = S.radau_reject = S.radau_newton = S.radau_dec = 0;
+  S.radau_alg_flops = 0.0;
+  // device time from the start event (which every instance stream waits on)
+  // to the end event (which waits on every instance stream)
+  if (cudaEventRecord(b->ev_start, b->stream) != cudaSuccess) return MR_ECUDA;
+  for (int i = 0; i < b->n; i++)
+    if (cudaStreamWaitEvent(b->streams[i], b->ev_start, 0) != cudaSuccess) return MR_ECUDA;
+  mr_status s = MR_OK;
+  for (int step = 0; step < nsteps && !s; step++) {
+    s = for_all(b, [&](int i) {
+      mr_status r = adapt(b->ctx[i], eta[i]);
+      return r ? r : build_tables(b->ctx[i]);
+    });
+    if (s) break;
+    for (mr_ctx* c : b->ctx) S.leaf_updates += c->tb[c->cur].nleaves;
+    s = react_all(b, 0.5 * dt, rtol, atol);
+    if (s) break;
+    s = for_all(b, [&](int i) { return diffuse(b->ctx[i], dt, rock_tol); });
+    if (s) break;
+    s = react_all(b, 0.5 * dt, rtol, atol);
+    S.steps++;
+  }
+  for (int i = 0; i < b->n; i++) {
+    cudaEventRecord(b->ev[i], b->streams[i]);
+    cudaStreamWaitEvent(b->stream, b->ev[i], 0);
+  }
+  cudaEventRecord(b->ev_end, b->stream);
+  if (cudaEventSynchronize(b->ev_end) != cudaSuccess && !s) s = MR_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->ev_start, b->ev_end);
+  S.ms_device = ms;
+  if (s) b->last_error = "a batched step failed (see the instance contexts' last errors)";
+  return s;
+}
+
+mr_status mr_batch_get_stats(const mr_batch* b, mr_batch_stats* out) {
+  if (!b || !out) return MR_EINVAL;
+  *out = b->stats;
+  return MR_OK;
+}
+
+void mr_batch_destroy(mr_batch* b) {
+  if (b) batch_free(b);
+}
+
+}  // extern "C"

@@ -223,6 +223,21 @@ mr_status sync_counts(mr_ctx* c);
 void radau_constants(double* rc);
 mr_status react(mr_ctx* c, double dt, double rtol, double atol);
 
+// Reaction sub-step of several contexts (same model kind and precision, one
+// thread per cell models) as one persistent launch over the union of their
+// leaves, on `stream`.  The caller owns the scratch; counters[7] receives the
+// summed Radau5 counters, *kernel_ms the launch's device time.
+struct BatchReactScratch {
+  DevCounters* dc = nullptr;
+  void* inst = nullptr;     // per-instance model, state and complexity arrays (device)
+  int64_t* offs = nullptr;  // prefix offsets of the instances' leaf counts (device)
+  int cap = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double atol, cudaStream_t stream,
+                      BatchReactScratch& S, double* kernel_ms, unsigned long long* counters);
+void free_batch_scratch(BatchReactScratch& S);
+
 // rock4.cu
 int rock4_coeffs(int s, double* mu, double* nu, double* kap, double* w, double* errc);
 double rock4_ell(int s);

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <complex>
 #include <mutex>
+#include <vector>
 #include <math.h>
 #include <string.h>
 
@@ -216,11 +217,37 @@ __device__ inline void sol_cplx(const T* ar, const T* ai, const int* piv, const 
 //
 // LT: arithmetic of the factorisations and solves (double, or float for the
 // mixed form: residuals, norms, error estimate and step control stay double)
+// The cells of several independent instances (batched serving): instance b
+// owns queue positions [offs[b], offs[b + 1]) and has its own model
+// parameters, state array and complexity array.
+template <class Mdl>
+struct BatchInst {
+  Mdl md;
+  double* U;
+  int64_t capL;
+  int32_t* complexity;
+};
+
+// One context is a batch of one, passed by value in `one` (inst == nullptr),
+// so that a context stepped alone and one stepped in a batch run the same
+// compiled arithmetic.
+template <class Mdl>
+struct BatchCells {
+  const BatchInst<Mdl>* inst;
+  const int64_t* offs;  // n + 1 prefix offsets of the instances' leaf counts
+  int n;
+  BatchInst<Mdl> one;
+};
+
 template <class Mdl, typename LT = double>
-__global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restrict__ U, int64_t N,
-                                               int64_t capL, double tend,
-                                               int32_t* __restrict__ complexity, DevCounters* dc) {
+__global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int64_t N, double tend,
+                                               DevCounters* dc) {
   constexpr int M = Mdl::M;
+  // the instance of the current cell
+  Mdl mdl = B.one.md;
+  double* Ub = B.one.U;
+  int64_t capLb = B.one.capL;
+  int32_t* cxb = B.one.complexity;
   const double uround = 1e-16;
   const int kmax = 7;
   const double safe = 0.9, thet = 0.001, facl = 5.0, facr = 0.125, quot1 = 1.0, quot2 = 1.2;
@@ -253,8 +280,24 @@ __global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restr
     if (cell < 0) {
       cell = atomicAdd(&dc->work_next, 1);
       if (cell >= N) break;
+      if (B.inst) {
+        int lo = 0, hi = B.n - 1;  // last instance with offs[b] <= cell
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (B.offs[mid] <= cell)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const BatchInst<Mdl>& I = B.inst[lo];
+        mdl = I.md;
+        Ub = I.U;
+        capLb = I.capL;
+        cxb = I.complexity;
+        cell -= (int)B.offs[lo];
+      }
 #pragma unroll
-      for (int i = 0; i < M; i++) y[i] = U[i * capL + cell];
+      for (int i = 0; i < M; i++) y[i] = Ub[i * capLb + cell];
       n = CellCount{0, 0, 0, 0, 0, 0, 0};
       t = 0.0;
       h = tend;
@@ -271,13 +314,13 @@ __global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restr
       hacc = 0.0;
       erracc = 0.0;
       theta = thet;
-      md.rhs(y, f0);
+      mdl.rhs(y, f0);
       n.nfev++;
       phase = P_TOP;
     }
     if (phase == P_TOP) {
       if (need_jac) {
-        md.jac(y, J);
+        mdl.jac(y, J);
         n.njac++;
         jac_fresh = true;
         need_jac = false;
@@ -376,7 +419,7 @@ __global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restr
         for (int s = 0; s < 3; s++) {
 #pragma unroll
           for (int i = 0; i < M; i++) tmp[i] = y[i] + Z[s][i];
-          md.rhs(tmp, F[s]);
+          mdl.rhs(tmp, F[s]);
         }
         n.nfev += 3;
         double r1[M], r2[M], r3[M];
@@ -485,7 +528,7 @@ __global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restr
           double tmp[M], fe[M];
 #pragma unroll
           for (int i = 0; i < M; i++) tmp[i] = y[i] + ev[i];
-          md.rhs(tmp, fe);
+          mdl.rhs(tmp, fe);
           n.nfev++;
 #pragma unroll
           for (int i = 0; i < M; i++) ev[i] = fe[i] + g0 * Z[0][i] + g1 * Z[1][i] + g2 * Z[2][i];
@@ -527,7 +570,7 @@ __global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restr
             finish = true;
           } else {
             t += h;
-            md.rhs(y, f0);
+            mdl.rhs(y, f0);
             n.nfev++;
             if (reject) hnew = fmin(hnew, h);
             reject = false;
@@ -561,8 +604,8 @@ __global__ void __launch_bounds__(128) k_radau(Mdl md, RadauC C, double* __restr
     }
     if (finish) {
 #pragma unroll
-      for (int i = 0; i < M; i++) U[i * capL + cell] = y[i];
-      if (complexity) complexity[cell] = n.nfev + M * n.njac;
+      for (int i = 0; i < M; i++) Ub[i * capLb + cell] = y[i];
+      if (cxb) cxb[cell] = n.nfev + M * n.njac;
       if (st) atomicCAS(&dc->status, 0, st);
       acc[0] += n.nfev;
       acc[1] += n.njac;
@@ -758,18 +801,19 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   if (grid < 1) grid = 1;
   MR_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
   if (c->prob.model == MR_MODEL_BZ) {
-    BZ md{1.0 / c->prob.params[1], 1.0 / c->prob.params[0], c->prob.params[2], c->prob.params[3]};
+    const BZ md{1.0 / c->prob.params[1], 1.0 / c->prob.params[0], c->prob.params[2], c->prob.params[3]};
+    const BatchCells<BZ> B{nullptr, nullptr, 1, BatchInst<BZ>{md, t.U, c->cap_leaves, c->complexity}};
     if (mixed)
-      k_radau<BZ, float><<<grid, 128, 0, c->stream>>>(md, C, t.U, N, c->cap_leaves, dt, c->complexity, c->dc);
+      k_radau<BZ, float><<<grid, 128, 0, c->stream>>>(B, C, N, dt, c->dc);
     else
-      k_radau<BZ, double><<<grid, 128, 0, c->stream>>>(md, C, t.U, N, c->cap_leaves, dt, c->complexity, c->dc);
+      k_radau<BZ, double><<<grid, 128, 0, c->stream>>>(B, C, N, dt, c->dc);
   } else {
-    Nagumo md{c->prob.params[0]};
+    const Nagumo md{c->prob.params[0]};
+    const BatchCells<Nagumo> B{nullptr, nullptr, 1, BatchInst<Nagumo>{md, t.U, c->cap_leaves, c->complexity}};
     if (mixed)
-      k_radau<Nagumo, float><<<grid, 128, 0, c->stream>>>(md, C, t.U, N, c->cap_leaves, dt, c->complexity, c->dc);
+      k_radau<Nagumo, float><<<grid, 128, 0, c->stream>>>(B, C, N, dt, c->dc);
     else
-      k_radau<Nagumo, double><<<grid, 128, 0, c->stream>>>(md, C, t.U, N, c->cap_leaves, dt, c->complexity,
-                                                           c->dc);
+      k_radau<Nagumo, double><<<grid, 128, 0, c->stream>>>(B, C, N, dt, c->dc);
   }
   c->launches++;
   MR_CUDA(c, cudaEventRecord(c->ev[6], c->stream));
@@ -797,6 +841,101 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   s.radau_newton = c->hc.radau[5];
   s.radau_dec = c->hc.radau[6];
   return (mr_status)c->hc.status;
+}
+
+// ------------------------------------------------------------ batched reaction
+namespace {
+template <class Mdl, typename LT>
+mr_status launch_batch(mr_ctx* const* cs, int n, const Mdl* mds, const RadauC& C, double dt, cudaStream_t stream,
+                       BatchReactScratch& S, int64_t total) {
+  std::vector<BatchInst<Mdl>> hin(n);
+  for (int b = 0; b < n; b++) {
+    TreeBuf& t = cs[b]->tb[cs[b]->cur];
+    hin[b] = BatchInst<Mdl>{mds[b], t.U, cs[b]->cap_leaves, cs[b]->complexity};
+  }
+  if (cudaMemcpyAsync(S.inst, hin.data(), sizeof(BatchInst<Mdl>) * n, cudaMemcpyHostToDevice, stream) !=
+      cudaSuccess)
+    return MR_ECUDA;
+  int dev = 0, nsm = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radau<Mdl, LT>, 128, 0);
+  per_sm = std::max(per_sm, 1);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, (int64_t)nsm * per_sm));
+  BatchCells<Mdl> B{reinterpret_cast<const BatchInst<Mdl>*>(S.inst), S.offs, n, hin[0]};
+  cudaEventRecord(S.ev[0], stream);
+  k_radau<Mdl, LT><<<grid, 128, 0, stream>>>(B, C, total, dt, S.dc);
+  cudaEventRecord(S.ev[1], stream);
+  return cudaGetLastError() == cudaSuccess ? MR_OK : MR_ECUDA;
+}
+}  // namespace
+
+void free_batch_scratch(BatchReactScratch& S) {
+  cudaFree(S.dc);
+  cudaFree(S.inst);
+  cudaFree(S.offs);
+  for (int q = 0; q < 2; q++)
+    if (S.ev[q]) cudaEventDestroy(S.ev[q]);
+  S = BatchReactScratch{};
+}
+
+mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double atol, cudaStream_t stream,
+                      BatchReactScratch& S, double* kernel_ms, unsigned long long* counters) {
+  if (n < 1) return MR_EINVAL;
+  const int model = cs[0]->prob.model, prec = cs[0]->prob.precision;
+  if (model != MR_MODEL_BZ && model != MR_MODEL_NAGUMO) return MR_EINVAL;
+  for (int b = 1; b < n; b++)
+    if (cs[b]->prob.model != model || cs[b]->prob.precision != prec) return MR_EINVAL;
+  if (S.cap < n) {
+    free_batch_scratch(S);
+    const size_t inst_bytes = std::max(sizeof(BatchInst<BZ>), sizeof(BatchInst<Nagumo>)) * n;
+    if (cudaMalloc(&S.dc, sizeof(DevCounters)) != cudaSuccess || cudaMalloc(&S.inst, inst_bytes) != cudaSuccess ||
+        cudaMalloc(&S.offs, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+        cudaEventCreate(&S.ev[0]) != cudaSuccess || cudaEventCreate(&S.ev[1]) != cudaSuccess) {
+      free_batch_scratch(S);
+      return MR_ENOMEM;
+    }
+    S.cap = n;
+  }
+  std::vector<int64_t> offs(n + 1, 0);
+  for (int b = 0; b < n; b++) offs[b + 1] = offs[b] + cs[b]->tb[cs[b]->cur].nleaves;
+  const int64_t total = offs[n];
+  if (total > INT32_MAX) return MR_EINVAL;
+  RadauC C = constants_from(cs[0]->rc);
+  C.rt = 0.1 * pow(rtol, 2.0 / 3.0);
+  C.at = C.rt * (atol / rtol);
+  C.fnewt = std::max(10.0 * 1e-16 / C.rt, std::min(0.03, sqrt(C.rt)));
+  if (cudaMemsetAsync(S.dc, 0, sizeof(DevCounters), stream) != cudaSuccess ||
+      cudaMemcpyAsync(S.offs, offs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, stream) !=
+          cudaSuccess)
+    return MR_ECUDA;
+  mr_status st;
+  const bool mixed = prec == MR_MIXED;
+  if (model == MR_MODEL_BZ) {
+    std::vector<BZ> mds(n);
+    for (int b = 0; b < n; b++) {
+      const double* p = cs[b]->prob.params;
+      mds[b] = BZ{1.0 / p[1], 1.0 / p[0], p[2], p[3]};
+    }
+    st = mixed ? launch_batch<BZ, float>(cs, n, mds.data(), C, dt, stream, S, total)
+               : launch_batch<BZ, double>(cs, n, mds.data(), C, dt, stream, S, total);
+  } else {
+    std::vector<Nagumo> mds(n);
+    for (int b = 0; b < n; b++) mds[b] = Nagumo{cs[b]->prob.params[0]};
+    st = mixed ? launch_batch<Nagumo, float>(cs, n, mds.data(), C, dt, stream, S, total)
+               : launch_batch<Nagumo, double>(cs, n, mds.data(), C, dt, stream, S, total);
+  }
+  if (st) return st;
+  DevCounters hc;
+  if (cudaMemcpyAsync(&hc, S.dc, sizeof hc, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return MR_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, S.ev[0], S.ev[1]);
+  if (kernel_ms) *kernel_ms = ms;
+  if (counters)
+    for (int q = 0; q < 7; q++) counters[q] = hc.radau[q];
+  return (mr_status)hc.status;
 }
 
 // ------------------------------------------------------------ no-allocation variant
@@ -850,10 +989,12 @@ mr_status react_noalloc(int model, const double* params, int nparams, double* u,
   int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)nsm * 8);
   if (model == MR_MODEL_BZ) {
     BZ md{1.0 / params[1], 1.0 / params[0], params[2], params[3]};
-    k_radau<BZ><<<grid, 128, 0, stream>>>(md, C, u, n, ld, dt, complexity, dc);
+    const BatchCells<BZ> B{nullptr, nullptr, 1, BatchInst<BZ>{md, u, ld, complexity}};
+    k_radau<BZ><<<grid, 128, 0, stream>>>(B, C, n, dt, dc);
   } else {
     Nagumo md{params[0]};
-    k_radau<Nagumo><<<grid, 128, 0, stream>>>(md, C, u, n, ld, dt, complexity, dc);
+    const BatchCells<Nagumo> B{nullptr, nullptr, 1, BatchInst<Nagumo>{md, u, ld, complexity}};
+    k_radau<Nagumo><<<grid, 128, 0, stream>>>(B, C, n, dt, dc);
   }
   if (cudaGetLastError() != cudaSuccess) return MR_ECUDA;
   int status = 0;

@@ -86,6 +86,9 @@ def lib():
             "mr_save": [vp, C.c_char_p],
             "mr_set_network": [vp, C.c_int, vp, dp, dp],
             "mr_load": [vp, C.c_char_p],
+            "mr_batch_create": [C.c_int, C.POINTER(Problem), C.c_int, C.POINTER(C.c_void_p)],
+            "mr_batch_run": [vp, C.c_int, C.c_double, dp, C.c_double, C.c_double, C.c_double],
+            "mr_batch_get_stats": [vp, C.POINTER(BatchStats)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -93,10 +96,25 @@ def lib():
             f.restype = C.c_int
         L.mr_destroy.argtypes = [vp]
         L.mr_destroy.restype = None
+        L.mr_batch_context.argtypes = [vp, C.c_int]
+        L.mr_batch_context.restype = C.c_void_p
+        L.mr_batch_destroy.argtypes = [vp]
+        L.mr_batch_destroy.restype = None
         L.mr_status_str.argtypes = [C.c_int]
         L.mr_status_str.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+class BatchStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("instances", "threads", "steps", "leaf_updates")] + \
+               [("ms_device", C.c_double), ("ms_react_kernel", C.c_double), ("react_launches", C.c_int64)] + \
+               [(n, C.c_int64) for n in ("radau_fev", "radau_jac", "radau_steps", "radau_accept", "radau_reject",
+                                         "radau_newton", "radau_dec")] + \
+               [("radau_alg_flops", C.c_double), ("joint_reaction", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
 
 
 class MRError(RuntimeError):
@@ -148,9 +166,17 @@ class Context:
             raise MRError(rc, "mr_create")
         self.h, self.prob, self.m = h, prob, prob.m
 
+    @classmethod
+    def _borrowed(cls, handle, prob):
+        """A view of a context owned by something else (a Batch): not destroyed on close."""
+        c = cls.__new__(cls)
+        c.h, c.prob, c.m, c._owned = C.c_void_p(handle), prob, prob.m, False
+        return c
+
     def close(self):
         if getattr(self, "h", None):
-            lib().mr_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lib().mr_destroy(self.h)
             self.h = None
 
     __del__ = close
@@ -265,3 +291,47 @@ def fp64_fma_rate():
     if rc:
         raise MRError(rc, "mr_fp64_fma_rate")
     return t.value, mhz.value
+
+
+class Batch:
+    """Batched serving (mr_batch_*): independent instances stepped together,
+    the reaction half steps of all of them as one joint Radau5 launch."""
+
+    def __init__(self, problems, threads=0):
+        arr = (Problem * len(problems))(*problems)
+        h = C.c_void_p()
+        rc = lib().mr_batch_create(len(problems), arr, threads, C.byref(h))
+        if rc:
+            raise MRError(rc, "mr_batch_create")
+        self.h, self.n = h, len(problems)
+        self.contexts = [Context._borrowed(lib().mr_batch_context(h, i), problems[i]) for i in range(self.n)]
+
+    def __getitem__(self, i):
+        return self.contexts[i]
+
+    def run(self, nsteps, dt, eta, rtol=1e-6, atol=1e-6, rock_tol=1e-6):
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        assert len(eta) == self.n
+        rc = lib().mr_batch_run(self.h, nsteps, dt, C.c_void_p(eta.ctypes.data), rtol, atol, rock_tol)
+        if rc:
+            msgs = []
+            for i, c in enumerate(self.contexts):
+                buf = C.create_string_buffer(256)
+                lib().mr_last_error(c.h, buf, 256)
+                if buf.value:
+                    msgs.append(f"[{i}] {buf.value.decode()}")
+            raise MRError(rc, "mr_batch_run", "; ".join(msgs))
+
+    def stats(self):
+        s = BatchStats()
+        lib().mr_batch_get_stats(self.h, C.byref(s))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            for c in self.contexts:
+                c.h = None
+            lib().mr_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close

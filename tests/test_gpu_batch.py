@@ -1,0 +1,108 @@
+"""Batched serving (mr_batch_*): instances stepped together give exactly the
+results of stepping each instance alone (the joint Radau5 launch integrates
+every cell with the same arithmetic), the counters add up, models that cannot
+share a launch fall back to per-instance launches, and one instance is
+checked against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1506_04651_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1506_04651_gb300 import mr as M
+    return M
+
+
+def instances(n):
+    out = []
+    for inst in I.batch_instances(n, master_seed=77):
+        inst = dict(inst, J=min(inst["J"], 8))
+        u0 = I.bz_front_smooth_2d(inst["J"], inst["seed"] & 0xFFFFFFFF, x0=inst["x0"], f=inst["f"])
+        out.append((inst, u0))
+    return out
+
+
+def problem(mr, inst):
+    return mr.problem(2, inst["J"], params=(1e-2, 1e-5, inst["f"], 2e-3))
+
+
+def test_batch_equals_separate_contexts(mr):
+    insts = instances(6)
+    b = mr.Batch([problem(mr, i) for i, _ in insts], threads=4)
+    singles = []
+    for k, (inst, u0) in enumerate(insts):
+        b[k].build(u0, inst["eta"])
+        c = mr.Context(problem(mr, inst))
+        c.build(u0, inst["eta"])
+        singles.append(c)
+    eta = [i["eta"] for i, _ in insts]
+    b.run(3, 1e-3, eta)
+    st = b.stats()
+    assert st["joint_reaction"] == 1 and st["steps"] == 3 and st["react_launches"] == 6
+    assert st["radau_fev"] > 0 and st["radau_newton"] > 0 and st["ms_device"] > 0
+    updates = 0
+    for _ in range(3):
+        for c, (inst, _) in zip(singles, insts):
+            c.strang(1e-3, inst["eta"])
+            updates += c.num_leaves()
+    assert st["leaf_updates"] == updates
+    for k, c in enumerate(singles):
+        kb, vb = b[k].leaves()
+        ks, vs = c.leaves()
+        assert np.array_equal(kb, ks) and np.array_equal(vb, vs)
+    b.close()
+
+
+def test_batch_instance_matches_oracle(mr):
+    inst, u0 = instances(1)[0]
+    b = mr.Batch([problem(mr, inst)])
+    b[0].build(u0, inst["eta"])
+    T = O.Tree(2, inst["J"], 3, jmin=2)
+    T.set_full(u0)
+    assert T.adapt(inst["eta"]) == 0
+    md = O.make_model("bz", params=(1e-2, 1e-5, inst["f"], 2e-3))
+    b.run(1, 1e-3, [inst["eta"]])
+    assert T.strang(md, I.BZ_D, 1e-3, inst["eta"]) == 0
+    k_o, v_o = T.leaves()
+    k_g, v_g = b[0].leaves()
+    assert np.array_equal(k_o, k_g)
+    for i in range(3):
+        assert np.max(np.abs(v_g[i] - v_o[i])) <= 1e-9 * np.max(np.abs(v_o[i]))
+
+
+def test_mixed_models_fall_back_per_instance(mr):
+    inst, u0 = instances(1)[0]
+    pn = mr.problem(2, 6, model="nagumo")
+    b = mr.Batch([problem(mr, inst), pn])
+    b[0].build(u0, inst["eta"])
+    x = (np.arange(64) + 0.5) / 64
+    un = (0.5 * (1 - np.tanh((np.add.outer(x * 0, x) - 0.5) / 0.05))).reshape(1, -1)
+    b[1].build(un, 1e-3)
+    cn = mr.Context(pn)
+    cn.build(un, 1e-3)
+    b.run(2, 1e-3, [inst["eta"], 1e-3])
+    assert b.stats()["joint_reaction"] == 0
+    for _ in range(2):
+        cn.strang(1e-3, 1e-3)
+    kb, vb = b[1].leaves()
+    ks, vs = cn.leaves()
+    assert np.array_equal(kb, ks) and np.array_equal(vb, vs)
+
+
+def test_batch_rejects_bad_arguments(mr):
+    inst, u0 = instances(1)[0]
+    b = mr.Batch([problem(mr, inst)])
+    b[0].build(u0, inst["eta"])
+    with pytest.raises(mr.MRError) as e:
+        b.run(1, 1e-3, [-1.0])
+    assert e.value.code == -1
+    with pytest.raises(mr.MRError) as e:
+        b.run(1, -1e-3, [1e-3])
+    assert e.value.code == -1
