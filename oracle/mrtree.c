@@ -680,32 +680,66 @@ int orc_apply_literal(orc_tree *T, const double *u, double *out) {
 
 /* ---------------- reaction, diffusion, Strang, mass ---------------- */
 
+/* every leaf integrates its own ODE: a parallel-for over the leaves (in leaf
+ * order); per-chunk counters and first errors are combined in chunk order, so
+ * the outcome is that of the serial loop */
+typedef struct {
+  orc_tree *T;
+  const orc_model *md;
+  double dt, rtol, atol;
+  int32_t *complexity;
+  int32_t (*leaf)[2]; /* (level, position) of every leaf, in leaf order */
+  orc_radau_stats *part;
+} react_args;
+
+static void react_leaves(void *p, int64_t lo, int64_t hi, int chunk) {
+  react_args *a = (react_args *)p;
+  orc_tree *T = a->T;
+  const int m = T->m;
+  orc_radau_stats *agg = &a->part[chunk];
+  double y[ORC_MAXM];
+  for (int64_t q = lo; q < hi; q++) {
+    const int j = a->leaf[q][0];
+    const int64_t pos = a->leaf[q][1];
+    for (int i = 0; i < m; i++) y[i] = T->v[j][(int64_t)i * T->n[j] + pos];
+    orc_radau_stats st;
+    int rc = orc_radau5(a->md, y, a->dt, a->rtol, a->atol, 0.0, &st);
+    if (rc && agg->status == ORC_OK) agg->status = rc;
+    for (int i = 0; i < m; i++) T->v[j][(int64_t)i * T->n[j] + pos] = y[i];
+    if (a->complexity) a->complexity[q] = (int32_t)(st.nfev + (int64_t)m * st.njac);
+    agg->nfev += st.nfev; agg->njac += st.njac; agg->nstep += st.nstep;
+    agg->naccept += st.naccept; agg->nreject += st.nreject;
+    agg->nnewton += st.nnewton; agg->ndec += st.ndec;
+  }
+}
+
 int orc_react(orc_tree *T, const orc_model *md, double dt, double rtol, double atol,
               orc_radau_stats *agg, int32_t *complexity) {
   int64_t N = index_leaves(T);
-  (void)N;
-  const int m = T->m;
-  int status = ORC_OK;
-  double y[ORC_MAXM];
-  if (agg) memset(agg, 0, sizeof *agg);
+  int32_t (*leaf)[2] = malloc(sizeof(int32_t[2]) * (N > 0 ? N : 1));
   for (int j = 0; j <= T->J; j++)
     for (int64_t p = 0; p < T->n[j]; p++) {
       int32_t r = T->lidx[j][p];
       if (r < 0) continue;
-      for (int i = 0; i < m; i++) y[i] = T->v[j][(int64_t)i * T->n[j] + p];
-      orc_radau_stats st;
-      int rc = orc_radau5(md, y, dt, rtol, atol, 0.0, &st);
-      if (rc && status == ORC_OK) status = rc;
-      for (int i = 0; i < m; i++) T->v[j][(int64_t)i * T->n[j] + p] = y[i];
-      if (complexity) complexity[r] = (int32_t)(st.nfev + (int64_t)m * st.njac);
-      if (agg) {
-        agg->nfev += st.nfev; agg->njac += st.njac; agg->nstep += st.nstep;
-        agg->naccept += st.naccept; agg->nreject += st.nreject;
-        agg->nnewton += st.nnewton; agg->ndec += st.ndec;
-      }
+      leaf[r][0] = j;
+      leaf[r][1] = (int32_t)p;
     }
-  if (agg) agg->status = status;
-  return status;
+  const int64_t chunk = 64, nchunks = (N + chunk - 1) / chunk;
+  orc_radau_stats *part = calloc(nchunks > 0 ? nchunks : 1, sizeof(orc_radau_stats));
+  react_args a = {T, md, dt, rtol, atol, complexity, leaf, part};
+  orc_parallel_for(N, chunk, react_leaves, &a);
+  orc_radau_stats tot;
+  memset(&tot, 0, sizeof tot);
+  for (int64_t q = 0; q < nchunks; q++) {
+    if (part[q].status && tot.status == ORC_OK) tot.status = part[q].status;
+    tot.nfev += part[q].nfev; tot.njac += part[q].njac; tot.nstep += part[q].nstep;
+    tot.naccept += part[q].naccept; tot.nreject += part[q].nreject;
+    tot.nnewton += part[q].nnewton; tot.ndec += part[q].ndec;
+  }
+  free(part);
+  free(leaf);
+  if (agg) *agg = tot;
+  return tot.status;
 }
 
 int orc_diffuse(orc_tree *T, const double *D, double dt, double tol, orc_rock_stats *agg) {

@@ -20,6 +20,8 @@
  *   rock4.c   ROCK4-type stabilized polynomials and the linear diffusion
  *             integrator (Sec. 3.2.1, Eq. (RKscheme), Horner form; Abdulle's
  *             construction cited as MR1923724)
+ *   parallel.c a parallel-for (one chunk per thread) for the threaded form of
+ *             the timed CPU baseline; one thread by default
  *   mrtree.c  dyadic tree, projection, prediction (Eq. inter_1d), details
  *             (Eq. detail), thresholds, graded refinement and coarsening
  *             (Sec. 2.2, Sec. 3.1.2), finite-volume leaf operator (Eq.
@@ -65,6 +67,13 @@ typedef struct {
   int64_t nsteps, naccept, nreject, nstages, nmatvec;
   int smax, status;
 } orc_rock_stats;
+
+/* ---- parallel.c (threaded form of the timed CPU baseline only) ---- */
+typedef void (*orc_body)(void *ctx, int64_t lo, int64_t hi, int chunk);
+void orc_set_threads(int t);
+int orc_get_threads(void);
+/* body(ctx, lo, hi, chunk index) over chunks of `chunk` iterations */
+void orc_parallel_for(int64_t n, int64_t chunk, orc_body body, void *ctx);
 
 /* ---- radau5.c ---- */
 void orc_model_f(const orc_model *md, const double *y, double *f);

@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = ["radau5.c", "rock4.c", "mrtree.c"]
+_SRC = ["radau5.c", "rock4.c", "mrtree.c", "parallel.c"]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC",
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC", "-pthread",
            "-shared", "-o", tmp] + [os.path.join(_HERE, s) for s in _SRC] + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -127,6 +127,11 @@ def _l(a):
 
 def _u(a):
     return a.ctypes.data_as(C.POINTER(C.c_uint64))
+
+
+def set_threads(n: int):
+    """Threads of the oracle's parallel-for (reaction leaves, operator rows); 1 = the plain serial loops."""
+    lib().orc_set_threads(int(n))
 
 
 def make_model(kind: str, m: int | None = None, params=None, K=None) -> Model:

@@ -185,13 +185,28 @@ int orc_rock4_choose(double rho_dt, int *s, double *ell) {
   return 1;
 }
 
+typedef struct {
+  const int64_t *rp;
+  const int32_t *col;
+  const double *val, *x;
+  double scale, *y;
+} mv_args;
+
+static void matvec_rows(void *p, int64_t lo, int64_t hi, int chunk) {
+  const mv_args *a = (const mv_args *)p;
+  (void)chunk;
+  for (int64_t r = lo; r < hi; r++) {
+    double acc = 0.0;
+    for (int64_t e = a->rp[r]; e < a->rp[r + 1]; e++) acc += a->val[e] * a->x[a->col[e]];
+    a->y[r] = a->scale * acc;
+  }
+}
+
+/* y = scale * (A x), rows independent (parallel-for over rows) */
 static void matvec(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                    double scale, const double *x, double *y) {
-  for (int64_t r = 0; r < n; r++) {
-    double acc = 0.0;
-    for (int64_t e = rp[r]; e < rp[r + 1]; e++) acc += val[e] * x[col[e]];
-    y[r] = scale * acc;
-  }
+  mv_args a = {rp, col, val, x, scale, y};
+  orc_parallel_for(n, 4096, matvec_rows, &a);
 }
 
 /*
