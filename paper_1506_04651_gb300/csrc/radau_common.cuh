@@ -14,6 +14,7 @@ struct RadauC {
   double ge[3];        // gam * e_j (embedded estimate weights times gam)
   double idn[4][4];    // 1 / (nd[a] - nd[b]) for the nodes (0, c1, c2, 1)
   double rt, at, fnewt;  // transformed tolerances and Newton tolerance (per call)
+  double ifnewt;         // 1 / fnewt
   double fac[8];       // min(0.9, 0.9 (1 + 2 kmax)/(k + 2 kmax)), k Newton iterations
 };
 
@@ -25,6 +26,21 @@ __device__ inline double clampd(double x, double lo, double hi) { return fmin(fm
 
 // x^(1/4) through two square roots (hardware-assisted) instead of pow
 __device__ inline double root4(double x) { return sqrt(sqrt(x)); }
+
+// x^0.8 (x in [1e-16, 100]) for the Newton-stopping factor of each step
+// attempt: an FP32 estimate refined by two FP64 Newton steps on y^5 = x^4,
+// within a few ulps of pow at a fraction of its FP64 instructions (the factor
+// only enters the comparison with the Newton tolerance)
+__device__ inline double pow08(double x) {
+  double y = (double)exp2f(0.8f * log2f((float)x));
+  const double x2 = x * x, x4 = x2 * x2;
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    const double y2 = y * y;
+    y = y + (x4 / (y2 * y2) - y) * 0.2;
+  }
+  return y;
+}
 
 // kernel-side constants from radau_constants' array (tolerances unset)
 RadauC constants_from(const double* rc);
