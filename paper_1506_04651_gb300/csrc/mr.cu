@@ -126,17 +126,56 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
                           Level L, int64_t nnodes, int m, int64_t capN, const double* __restrict__ scale,
                           const double* __restrict__ eps_j, uint8_t* __restrict__ tag,
                           double* __restrict__ delta_out, DevCounters* dc) {
+  // the 3^d prediction weights of each child parity, built in the order
+  // predict() multiplies them (they are products of 1 and +-1/8, exact)
+  constexpr int NST = D == 2 ? 9 : 27;
+  __shared__ double sw[1 << D][NST];
+  for (int q = threadIdx.x; q < (1 << D) * NST; q += blockDim.x) {
+    const int par = q / NST;
+    int oo = q % NST;
+    double w = 1.0;
+    for (int a = 0; a < D; a++) {
+      const int off = oo % 3 - 1;
+      oo /= 3;
+      w = __dmul_rn(w, wpred((par >> a) & 1, off));
+    }
+    sw[par][q % NST] = w;
+  }
+  __syncthreads();
   for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nnodes;
        n += (int64_t)gridDim.x * blockDim.x) {
     int j = lvl[n];
     int k[3];
     unmorton<D>(code[n], k);
     const int32_t* dm = dmap + L.doff[j - 1];
+    // the parent-level stencil, looked up once for all species
+    const int par[3] = {k[0] >> 1, k[1] >> 1, D == 3 ? k[2] >> 1 : 0};
+    const int parity = (k[0] & 1) | ((k[1] & 1) << 1) | (D == 3 ? (k[2] & 1) << 2 : 0);
+    int32_t idx[NST];
+    bool graded = true;
+#pragma unroll
+    for (int o = 0; o < NST; o++) {
+      int oo = o, q[3] = {0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < D; a++) {
+        q[a] = mirror(par[a] + oo % 3 - 1, j - 1);
+        oo /= 3;
+      }
+      idx[o] = dm[morton<D>(q)];
+      graded = graded && idx[o] >= 0;
+    }
     double dmax = 0.0;
-    for (int i = 0; i < m; i++) {
-      double p = predict<D>(V, dm, k, j - 1, capN, i);
-      double dd = fabs(__dadd_rn(V[i * capN + n], -p)) / scale[i];
-      dmax = fmax(dmax, dd);
+    if (!graded) {
+      dmax = __longlong_as_double(0x7ff8000000000000ll);  // a stencil cell is missing: NaN
+    } else {
+      for (int i = 0; i < m; i++) {
+        const double* Vi = V + i * capN;
+        double p = 0.0;  // same products and sums, in the same order, as predict()
+#pragma unroll
+        for (int o = 0; o < NST; o++) p = __dadd_rn(p, __dmul_rn(sw[parity][o], Vi[idx[o]]));
+        double dd = fabs(__dadd_rn(Vi[n], -p)) / scale[i];
+        dmax = fmax(dmax, dd);
+      }
     }
     if (isnan(dmax)) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
     tag[n] = dmax >= eps_j[j];
@@ -479,21 +518,33 @@ struct IrrCfg<2> {
 };
 template <>
 struct IrrCfg<3> {
-  static constexpr int kCells = 1024, kSort = kIrrSlot3, kWarps = 2;
+  static constexpr int kCells = 1024, kSort = kIrrSlot3, kWarps = 3;
 };
+
+static_assert(sizeof(int32_t) * IrrCfg<2>::kSort + sizeof(double) * IrrCfg<2>::kSort <=
+                  sizeof(unsigned long long) * IrrCfg<2>::kCells &&
+              sizeof(int32_t) * IrrCfg<3>::kSort + sizeof(double) * IrrCfg<3>::kSort <=
+                  sizeof(unsigned long long) * IrrCfg<3>::kCells,
+              "a row's leaves fit in the key bytes");
 
 constexpr unsigned long long kEmptyCell = ~0ull;
 constexpr int32_t kAbsent = -1, kInternal = -2, kUnresolved = -3;
 
 template <int D>
 struct IrrShared {
-  unsigned long long key[IrrCfg<D>::kCells];  // (level << 48) | Morton code
+  // the keys are dead once every cell is resolved, and the row's leaves are
+  // collected into the same bytes for placement
+  union {
+    unsigned long long key[IrrCfg<D>::kCells];  // (level << 48) | Morton code
+    struct {
+      int32_t skey[IrrCfg<D>::kSort];
+      double sval[IrrCfg<D>::kSort];
+    } row;
+  };
   double w[IrrCfg<D>::kCells];
   int32_t st[IrrCfg<D>::kCells];  // leaf index, kAbsent or kInternal
   int16_t order[IrrCfg<D>::kCells];  // table slots in the order the cells were named
   int16_t list[IrrCfg<D>::kCells];   // slots of the cells one pass expands
-  int32_t skey[IrrCfg<D>::kSort];
-  double sval[IrrCfg<D>::kSort];
   int n, cnt, lo, hi, bad;
 };
 
@@ -681,8 +732,8 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
       if (S.st[h] >= 0 && S.w[h] != 0.0) {
         const int pos = atomicAdd(&S.cnt, 1);
         if (pos < kS) {
-          S.skey[pos] = S.st[h];
-          S.sval[pos] = S.w[h];
+          S.row.skey[pos] = S.st[h];
+          S.row.sval[pos] = S.w[h];
         } else {
           atomicExch(&S.bad, 1);
         }
@@ -696,24 +747,23 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
     double sa = 0.0;
     const bool ok = !S.bad && cntr <= slot;
     for (int q = lane; q < cntr; q += 32) {
-      const int32_t kq = S.skey[q];
+      const int32_t kq = S.row.skey[q];
       int rank = 0;
 #pragma unroll 8
-      for (int p = 0; p < cntr; p++) rank += S.skey[p] < kq;
-      sa += fabs(S.sval[q]);
+      for (int p = 0; p < cntr; p++) rank += S.row.skey[p] < kq;
+      sa += fabs(S.row.sval[q]);
       if (ok) {
         col[row * (int64_t)slot + rank] = kq;
-        wout[row * (int64_t)slot + rank] = S.sval[q];
-        wout_f[row * (int64_t)slot + rank] = (float)S.sval[q];
+        wout[row * (int64_t)slot + rank] = S.row.sval[q];
+        wout_f[row * (int64_t)slot + rank] = (float)S.row.sval[q];
       }
     }
     for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
-    // empty the table for the next row (only the slots this row used)
-    for (int e = lane; e < ne; e += 32) {
-      const int h = S.order[e];
-      S.key[h] = kEmptyCell;
-      S.w[h] = 0.0;
-    }
+    // empty the table for the next row: every key (the placement overwrote
+    // them), the weights of the slots this row used
+    __syncwarp();
+    for (int q = lane; q < kC; q += 32) S.key[q] = kEmptyCell;
+    for (int e = lane; e < ne; e += 32) S.w[S.order[e]] = 0.0;
     if (lane == 0) {
       cnt[row] = ok ? cntr : 0;
       if (!ok) atomicExch(&dc->overflow, 1);
