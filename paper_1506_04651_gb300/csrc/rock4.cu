@@ -378,9 +378,11 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     __syncthreads();
   };
   // one operator sweep: regular leaves one thread each from the compact
-  // table (neighbour indices loaded once for all species), merged rows four
+  // table (neighbour indices loaded once for all species), merged rows G
   // lanes each
-  constexpr int G = 4;
+  // lanes per merged row: 2D rows are short (~30 entries), 3D rows long
+  // (~100); measured best 2 and 4
+  constexpr int G = D == 2 ? 2 : 4;
   constexpr int MG = (M + G - 1) / G;  // species a merged-row lane finishes
   const int sub = lane & (G - 1);
   auto sweep = [&](double* err, double* err_row) {
