@@ -938,6 +938,10 @@ static void project(mr_ctx* c, const TreeBuf& t) {
 
 mr_status adapt(mr_ctx* c, double eta) {
   const int D = c->d, J = c->J, m = c->m;
+  // eta = 0 on the uniform finest grid (as many leaves as level-J cells):
+  // every node is tagged (delta >= 0 = eps_j) and no leaf can be refined or
+  // coarsened, so the adaptation is the identity and the tables stay valid
+  if (eta == 0.0 && c->tb[c->cur].nleaves == c->n_level[J]) return MR_OK;
   const int src = c->cur, dst = 1 - c->cur;
   TreeBuf& t = c->tb[src];
   Level L = make_level(c, t);
