@@ -101,9 +101,15 @@ __device__ inline void net_jac(const NetModel& N, const MyRx& X, double u, unsig
   }
 }
 
-// LU of the team's real matrix (row t in a[]), pivot order into pk[]
+// The Newton matrices live in shared memory, one padded row per lane (stride
+// kRow elements: the 16 lanes of a team hit 16 different banks in a column);
+// `a` is this lane's row and `a0` row 0 of the team, so that the pivot row of
+// a step is read directly (a broadcast) instead of through shuffles.
+constexpr int kRow = kTeam + 1;
+
+// LU of the team's real matrix, pivot order into pk[]
 template <typename T>
-__device__ inline bool team_lu_real(T (&a)[kTeam], int t, unsigned mask, int* pk, int& step, T& inv) {
+__device__ inline bool team_lu_real(T* a, const T* a0, int t, unsigned mask, int* pk, int& step, T& inv) {
   step = kTeam;
 #pragma unroll
   for (int k = 0; k < kTeam; k++) {
@@ -120,9 +126,7 @@ __device__ inline bool team_lu_real(T (&a)[kTeam], int t, unsigned mask, int* pk
     }
     if (!(cand > 0.0)) return false;
     if (t == 0) pk[k] = who;
-    T prow[kTeam];
-#pragma unroll
-    for (int j = k; j < kTeam; j++) prow[j] = __shfl_sync(mask, a[j], who, kTeam);
+    const T* prow = a0 + who * kRow;
     const T pinv = (T)1 / prow[k];
     if (t == who) {
       step = k;
@@ -133,14 +137,14 @@ __device__ inline bool team_lu_real(T (&a)[kTeam], int t, unsigned mask, int* pk
 #pragma unroll
       for (int j = k + 1; j < kTeam; j++) a[j] -= l * prow[j];
     }
+    __syncwarp(mask);
   }
-  __syncwarp(mask);
   return true;
 }
 
 template <typename T>
-__device__ inline bool team_lu_cplx(T (&ar)[kTeam], T (&ai)[kTeam], int t, unsigned mask, int* pk, int& step,
-                                    T& invr, T& invi) {
+__device__ inline bool team_lu_cplx(T* ar, T* ai, const T* ar0, const T* ai0, int t, unsigned mask, int* pk,
+                                    int& step, T& invr, T& invi) {
   step = kTeam;
 #pragma unroll
   for (int k = 0; k < kTeam; k++) {
@@ -157,12 +161,8 @@ __device__ inline bool team_lu_cplx(T (&ar)[kTeam], T (&ai)[kTeam], int t, unsig
     }
     if (!(cand > 0.0)) return false;
     if (t == 0) pk[k] = who;
-    T pr[kTeam], pi[kTeam];
-#pragma unroll
-    for (int j = k; j < kTeam; j++) {
-      pr[j] = __shfl_sync(mask, ar[j], who, kTeam);
-      pi[j] = __shfl_sync(mask, ai[j], who, kTeam);
-    }
+    const T* pr = ar0 + who * kRow;
+    const T* pi = ai0 + who * kRow;
     const T den = (T)1 / (pr[k] * pr[k] + pi[k] * pi[k]);
     const T qr = pr[k] * den, qi = -pi[k] * den;  // 1 / pivot
     if (t == who) {
@@ -175,19 +175,20 @@ __device__ inline bool team_lu_cplx(T (&ar)[kTeam], T (&ai)[kTeam], int t, unsig
       ai[k] = li;
 #pragma unroll
       for (int j = k + 1; j < kTeam; j++) {
-        ar[j] -= lr * pr[j] - li * pi[j];
-        ai[j] -= lr * pi[j] + li * pr[j];
+        const T prj = pr[j], pij = pi[j];
+        ar[j] -= lr * prj - li * pij;
+        ai[j] -= lr * pij + li * prj;
       }
     }
+    __syncwarp(mask);
   }
-  __syncwarp(mask);
   return true;
 }
 
 // solve with the team's real factors: b (component t of the right-hand side)
 // in, component t of the solution out
 template <typename T>
-__device__ inline T team_sol_real(const T (&a)[kTeam], int t, unsigned mask, const int* pk, int step, T inv, T b) {
+__device__ inline T team_sol_real(const T* a, int t, unsigned mask, const int* pk, int step, T inv, T b) {
 #pragma unroll
   for (int k = 0; k < kTeam; k++) {
     const T bp = __shfl_sync(mask, b, pk[k], kTeam);
@@ -204,8 +205,8 @@ __device__ inline T team_sol_real(const T (&a)[kTeam], int t, unsigned mask, con
 }
 
 template <typename T>
-__device__ inline void team_sol_cplx(const T (&ar)[kTeam], const T (&ai)[kTeam], int t, unsigned mask,
-                                     const int* pk, int step, T invr, T invi, T& br, T& bi) {
+__device__ inline void team_sol_cplx(const T* ar, const T* ai, int t, unsigned mask, const int* pk, int step,
+                                     T invr, T invi, T& br, T& bi) {
 #pragma unroll
   for (int k = 0; k < kTeam; k++) {
     const T pr = __shfl_sync(mask, br, pk[k], kTeam);
@@ -235,19 +236,31 @@ __device__ inline void team_sol_cplx(const T (&ar)[kTeam], const T (&ai)[kTeam],
 }
 
 template <typename LT>
-__global__ void __launch_bounds__(kTeamBlock) k_radau_team(NetModel N, RadauC C, double* __restrict__ U,
+__global__ void __launch_bounds__(kTeamBlock, 3) k_radau_team(NetModel N, RadauC C, double* __restrict__ U,
                                                            int64_t ncell, int64_t capL, double tend,
                                                            int32_t* __restrict__ complexity, DevCounters* dc) {
-  __shared__ double sJ[kTeamBlock / kTeam][kTeam][kTeam + 1];
-  __shared__ int sP1[kTeamBlock / kTeam][kTeam], sP2[kTeamBlock / kTeam][kTeam];
+  // dynamic shared memory: Jacobian rows (double), then the three Newton
+  // matrix rows (LT) of every lane, then the pivot orders
+  extern __shared__ __align__(16) unsigned char net_smem[];
+  double* sJ = reinterpret_cast<double*>(net_smem);
+  LT* sE1 = reinterpret_cast<LT*>(sJ + kTeamBlock * kRow);
+  LT* sE2r = sE1 + kTeamBlock * kRow;
+  LT* sE2i = sE2r + kTeamBlock * kRow;
+  int* sP = reinterpret_cast<int*>(sE2i + kTeamBlock * kRow);
   const int team = threadIdx.x / kTeam;
   const int t = threadIdx.x & (kTeam - 1);
   const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
   const int m = N.m;
   const bool real_species = t < m;
-  double* Jrow = sJ[team][t];
-  int* pk1 = sP1[team];
-  int* pk2 = sP2[team];
+  double* Jrow = sJ + threadIdx.x * kRow;
+  LT* E1 = sE1 + threadIdx.x * kRow;
+  LT* E2r = sE2r + threadIdx.x * kRow;
+  LT* E2i = sE2i + threadIdx.x * kRow;
+  const LT* E1_0 = sE1 + team * kTeam * kRow;
+  const LT* E2r_0 = sE2r + team * kTeam * kRow;
+  const LT* E2i_0 = sE2i + team * kTeam * kRow;
+  int* pk1 = sP + team * 2 * kTeam;
+  int* pk2 = pk1 + kTeam;
   const uint32_t pos = real_species ? N.pos[t] : 0u, neg = real_species ? N.neg[t] : 0u;
   MyRx X;
 #pragma unroll
@@ -271,7 +284,6 @@ __global__ void __launch_bounds__(kTeamBlock) k_radau_team(NetModel N, RadauC C,
 
   // state of the cell this team holds (component t)
   double y = 0.0, f0 = 0.0;
-  LT E1[kTeam], E2r[kTeam], E2i[kTeam];
   LT i1 = 0, i2r = 0, i2i = 0;
   int st1 = kTeam, st2 = kTeam;
   double Z[3], W[3], cz[3], ch = 0.0;
@@ -344,8 +356,9 @@ __global__ void __launch_bounds__(kTeamBlock) k_radau_team(NetModel N, RadauC C,
         E2i[j] = (LT)(dg ? ai : 0.0);
       }
       n.ndec++;
-      const bool ok1 = team_lu_real<LT>(E1, t, mask, pk1, st1, i1);
-      const bool ok2 = ok1 && team_lu_cplx<LT>(E2r, E2i, t, mask, pk2, st2, i2r, i2i);
+      __syncwarp(mask);
+      const bool ok1 = team_lu_real<LT>(E1, E1_0, t, mask, pk1, st1, i1);
+      const bool ok2 = ok1 && team_lu_cplx<LT>(E2r, E2i, E2r_0, E2i_0, t, mask, pk2, st2, i2r, i2i);
       if (!ok2) {
         if (++nsing > 5) {
           st = MR_ERADAU_SINGULAR;
@@ -578,18 +591,21 @@ mr_status react_network(mr_ctx* c, const RadauC& C, double dt) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const bool mixed = c->prob.precision == MR_MIXED;
   const void* kern = mixed ? (const void*)k_radau_team<float> : (const void*)k_radau_team<double>;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTeamBlock, 0);
+  const size_t smem = sizeof(double) * kTeamBlock * kRow + (mixed ? sizeof(float) : sizeof(double)) * 3 *
+                      kTeamBlock * kRow + sizeof(int) * 2 * kTeamBlock;
+  MR_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTeamBlock, smem);
   per_sm = std::max(per_sm, 1);
   const int64_t want = (N * kTeam + kTeamBlock - 1) / kTeamBlock;
   int grid = (int)std::min<int64_t>(want, (int64_t)nsm * per_sm);
   if (grid < 1) grid = 1;
   MR_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
   if (mixed)
-    k_radau_team<float><<<grid, kTeamBlock, 0, c->stream>>>(c->net, C, tb.U, N, c->cap_leaves, dt, c->complexity,
-                                                            c->dc);
+    k_radau_team<float><<<grid, kTeamBlock, smem, c->stream>>>(c->net, C, tb.U, N, c->cap_leaves, dt,
+                                                               c->complexity, c->dc);
   else
-    k_radau_team<double><<<grid, kTeamBlock, 0, c->stream>>>(c->net, C, tb.U, N, c->cap_leaves, dt,
-                                                             c->complexity, c->dc);
+    k_radau_team<double><<<grid, kTeamBlock, smem, c->stream>>>(c->net, C, tb.U, N, c->cap_leaves, dt,
+                                                                c->complexity, c->dc);
   c->launches++;
   MR_CUDA(c, cudaEventRecord(c->ev[6], c->stream));
   MR_CUDA(c, cudaGetLastError());
