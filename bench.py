@@ -190,6 +190,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def aggregate_replicas(pg, ms, leaves, dev):
+    """Replicas (one independent instance per rank): the job's time is the
+    slowest rank's, its work the leaf updates of all ranks.  pg is
+    torch.distributed (or None for one rank)."""
+    if pg is None:
+        return ms, leaves
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    n = torch.tensor([float(leaves)], dtype=torch.float64, device=dev)
+    pg.all_reduce(n, op=pg.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -311,15 +325,7 @@ def run_gpu(args, w):
         conservation = {"total_amount_rel_drift": float(abs(y1[-1] - y0[-1]) / abs(y0[-1])),
                         "moiety_max_drift_rel_to_total": float(np.max(np.abs(y1 - y0)) / abs(y0[-1])),
                         "moieties": int(len(basis)), "steps": args.steps}
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-        n = torch.tensor([float(leaves)], device=dev)
-        pg.all_reduce(n, op=pg.ReduceOp.SUM)
-        total_leaves = n.item()
-    else:
-        total_leaves = leaves
+    ms, total_leaves = aggregate_replicas(pg, ms, leaves, dev)
     value = total_leaves / (ms * 1e-3)
 
     # kernel-level roofline figures over the timed region
