@@ -76,6 +76,7 @@ mr_status alloc_all(mr_ctx* c) {
   A(c->fl_forced, c->cap_dense_int);
   A(c->fl_final, c->cap_dense_int);
   A(c->grank, c->cap_dense_int);
+  A(c->smap, c->cap_dense);
   A(c->tag, c->cap_nodes);
   int64_t big = std::max(std::max(c->cap_dense_int, c->cap_nodes), c->cap_leaves);
   A(c->scan_tmp, 2 * (big / 2048 + 4));
@@ -114,7 +115,7 @@ void free_all(mr_ctx* c) {
     cudaFree(t.dmap); cudaFree(t.leaf_node); cudaFree(t.U);
   }
   cudaFree(c->V); cudaFree(c->Vnew); cudaFree(c->fl_state); cudaFree(c->fl_forced);
-  cudaFree(c->fl_final); cudaFree(c->grank); cudaFree(c->tag); cudaFree(c->scan_tmp);
+  cudaFree(c->fl_final); cudaFree(c->grank); cudaFree(c->tag); cudaFree(c->smap); cudaFree(c->scan_tmp);
   cudaFree(c->itmp); cudaFree(c->nbr); cudaFree(c->leaf_lvl); cudaFree(c->irr_leaf); cudaFree(c->reg_tab);
   cudaFree(c->irr_cnt); cudaFree(c->irr_ptr); cudaFree(c->irr_col); cudaFree(c->irr_w); cudaFree(c->irr_wf);
   for (int q = 0; q < 6; q++) cudaFree(c->work[q]);

@@ -548,10 +548,21 @@ struct IrrShared {
   int n, cnt, lo, hi, bad;
 };
 
+// per cell of every level (dense, level offsets L.doff): the leaf index, -2
+// for an internal node, -1 for a cell that is not in the tree
 struct IrrMaps {
-  const int32_t* dmap;
-  const int32_t* node_leaf;
+  const int32_t* smap;
 };
+
+__global__ void k_status_map(const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
+                             const int32_t* __restrict__ node_leaf, Level L, int64_t nnodes,
+                             int32_t* __restrict__ smap) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nnodes;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t li = node_leaf[n];
+    smap[L.doff[lvl[n]] + code[n]] = li >= 0 ? li : -2;
+  }
+}
 
 // name a cell: shared memory only; its status (leaf, internal, absent) is
 // looked up afterwards for all the cells a pass named at once (resolve)
@@ -590,9 +601,7 @@ __device__ inline void resolve(IrrShared<D>& S, const IrrMaps& M, const Level& L
     const int h = S.order[e];
     const unsigned long long key = S.key[h];
     const int j = (int)(key >> 48);
-    const int32_t idx = M.dmap[L.doff[j] + (int64_t)(key & 0xffffffffffffull)];
-    const int32_t li = idx >= 0 ? M.node_leaf[idx] : -1;
-    S.st[h] = idx < 0 ? kAbsent : (li >= 0 ? li : kInternal);
+    S.st[h] = M.smap[L.doff[j] + (int64_t)(key & 0xffffffffffffull)];  // leaf, kInternal or kAbsent
   }
 }
 
@@ -600,13 +609,13 @@ template <int D>
 __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
     k_irr_rows(const int32_t* __restrict__ irr_leaf, int64_t nrows, const int32_t* __restrict__ leaf_node,
                const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
-               const int32_t* __restrict__ dmap, const int32_t* __restrict__ node_leaf, Level L, int slot,
+               const int32_t* __restrict__ smap, Level L, int slot,
                int32_t* __restrict__ cnt, int32_t* __restrict__ col, double* __restrict__ wout,
                float* __restrict__ wout_f, unsigned long long* rho_bits, DevCounters* dc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kC = IrrCfg<D>::kCells, kS = IrrCfg<D>::kSort;
   IrrShared<D>& S = reinterpret_cast<IrrShared<D>*>(smem_raw)[threadIdx.x >> 5];
-  const IrrMaps M{dmap, node_leaf};
+  const IrrMaps M{smap};
   const int lane = threadIdx.x & 31;
   for (int q = lane; q < kC; q += 32) {
     S.key[q] = kEmptyCell;
@@ -635,8 +644,7 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
       int q[3] = {k[0], k[1], k[2]};
       q[a] += sg;
       if (q[a] >= 0 && q[a] < lim) {  // homogeneous Neumann: no flux through the boundary
-        const int32_t idx = dmap[L.doff[j] + morton<D>(q)];
-        if (idx < 0 || node_leaf[idx] >= 0) {
+        if (smap[L.doff[j] + morton<D>(q)] != kInternal) {
           cell_add<D>(S, j, q, ih2);  // same-level leaf, or ghost by prediction
           cell_add<D>(S, j, k, -ih2);
         } else {
@@ -1056,19 +1064,24 @@ mr_status build_tables(mr_ctx* c) {
     int nsm = 152, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // status of every cell of every level, for one-load lookups while the
+    // rows are built
+    MR_CUDA(c, cudaMemsetAsync(c->smap, 0xff, sizeof(int32_t) * c->cap_dense, c->stream));
+    k_status_map<<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(t.code, t.lvl, t.node_leaf, L, t.nnodes, c->smap);
+    c->launches++;
     if (D == 2) {
       const size_t sm = sizeof(IrrShared<2>) * IrrCfg<2>::kWarps;
       MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       int grid = (int)std::min<int64_t>((nrows + IrrCfg<2>::kWarps - 1) / IrrCfg<2>::kWarps, (int64_t)nsm * 16);
       k_irr_rows<2><<<grid, 32 * IrrCfg<2>::kWarps, sm, c->stream>>>(
-          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, slot, c->irr_cnt, c->irr_col,
+          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, c->smap, L, slot, c->irr_cnt, c->irr_col,
           c->irr_w, c->irr_wf, c->rho_bits, c->dc);
     } else {
       const size_t sm = sizeof(IrrShared<3>) * IrrCfg<3>::kWarps;
       MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       int grid = (int)std::min<int64_t>((nrows + IrrCfg<3>::kWarps - 1) / IrrCfg<3>::kWarps, (int64_t)nsm * 16);
       k_irr_rows<3><<<grid, 32 * IrrCfg<3>::kWarps, sm, c->stream>>>(
-          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, t.dmap, t.node_leaf, L, slot, c->irr_cnt, c->irr_col,
+          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, c->smap, L, slot, c->irr_cnt, c->irr_col,
           c->irr_w, c->irr_wf, c->rho_bits, c->dc);
     }
     c->launches++;

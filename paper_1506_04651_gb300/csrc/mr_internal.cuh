@@ -141,6 +141,7 @@ struct mr_ctx {
   uint8_t* fl_forced = nullptr;
   uint8_t* fl_final = nullptr;
   int32_t* grank = nullptr;          // dense exclusive ranks of refined cells
+  int32_t* smap = nullptr;           // [cap_dense] per cell of every level: leaf index, -2 internal, -1 absent
   uint8_t* tag = nullptr;            // per node tag of the last detail pass
   int32_t* scan_tmp = nullptr;       // block partials for scans
   int32_t* itmp = nullptr;           // int scratch [cap_nodes]
