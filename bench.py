@@ -41,6 +41,10 @@ WORKLOADS = {
                              desc="2D BZ, J=10 (1024^2 finest), eta=1e-3, graded, two crossing "
                                   "tanh fronts (w=0.01) with smooth seeded position noise (8 modes, "
                                   "amplitude 0.1): ~10% of finest cells are leaves; dt=1e-3, FP64"),
+    "bz2d_J10_cm": dict(d=2, J=10, eta=0.0, dt=1e-3, gen="cross", seed=2, w=0.01, amp=0.1, oracle_J=8,
+                        desc="2D BZ on the uniform 1024^2 grid (Cartesian mesh: J=10, eta=0), the same crossing "
+                             "fronts as the adaptive J=10 workload, dt=1e-3, FP64: the CM side of the paper's "
+                             "MR-versus-CM comparison"),
     "bz2d_J7_uniform": dict(d=2, J=7, eta=0.0, dt=1e-3, gen="front", seed=1,
                             desc="2D BZ, uniform 128^2 (J=7, eta=0), tanh front + 1% seeded noise, "
                                  "dt=1e-3, FP64"),
