@@ -407,7 +407,10 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
         combine<VT>(o[i], r, (sx - (VT)(2 * D) * x[r]) * ih2, P.tol, err[i]);
       }
     }
-    const int64_t grp = tid / G, ngrp = nth / G;
+    // 2D: merged rows are taken from the last threads, which have no regular
+    // leaf when the leaves number fewer than the threads (fewer threads do
+    // both kinds of work)
+    const int64_t grp = (D == 2 ? nth - 1 - tid : tid) / G, ngrp = nth / G;
     const int64_t rounds = (nirr + ngrp - 1) / ngrp;
     for (int64_t k = 0; k < rounds; k++) {
       const int64_t row = grp + k * ngrp;
