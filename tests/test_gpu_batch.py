@@ -106,3 +106,32 @@ def test_batch_rejects_bad_arguments(mr):
     with pytest.raises(mr.MRError) as e:
         b.run(1, -1e-3, [1e-3])
     assert e.value.code == -1
+
+
+def test_full_batch_config_one_step(mr):
+    """The full batched configuration (64 instances, J in {7..10}, seeded f,
+    eta, front position): one batched step, the smallest, a median and the
+    largest instance checked against the oracle."""
+    import torch
+    insts = I.batch_instances(64)
+    b = mr.Batch([mr.problem(2, i["J"], params=(1e-2, 1e-5, i["f"], 2e-3)) for i in insts])
+    u0s = {}
+    for k, inst in enumerate(insts):
+        u0s[k] = I.bz_front_smooth_2d(inst["J"], inst["seed"] & 0xFFFFFFFF, x0=inst["x0"], f=inst["f"])
+        b[k].build(torch.from_numpy(u0s[k]).cuda(), inst["eta"])
+    b.run(1, 1e-3, [i["eta"] for i in insts])
+    assert b.stats()["joint_reaction"] == 1
+    order = sorted(range(64), key=lambda k: (insts[k]["J"], k))
+    for k in (order[0], order[32], order[-1]):
+        inst = insts[k]
+        T = O.Tree(2, inst["J"], 3, jmin=2)
+        T.set_full(u0s[k])
+        assert T.adapt(inst["eta"]) == 0
+        md = O.make_model("bz", params=(1e-2, 1e-5, inst["f"], 2e-3))
+        assert T.strang(md, I.BZ_D, 1e-3, inst["eta"]) == 0
+        k_o, v_o = T.leaves()
+        k_g, v_g = b[k].leaves()
+        assert np.array_equal(k_o, k_g)
+        for i in range(3):
+            assert np.max(np.abs(v_g[i] - v_o[i])) <= 1e-9 * np.max(np.abs(v_o[i]))
+    b.close()
