@@ -107,24 +107,25 @@ __device__ inline void net_jac(const NetModel& N, const MyRx& X, double u, unsig
 // a step is read directly (a broadcast) instead of through shuffles.
 constexpr int kRow = kTeam + 1;
 
+// Pivot choice in one team reduction: the key orders candidates by |a| (the
+// bits of a non-negative float order like the value; its last 4 bits give way
+// to the lane, lower lanes winning ties), so the pivot is the largest
+// candidate to about 19 bits -- partial pivoting needs no more.
+__device__ inline unsigned pivot_key(bool open, float mag, int t) {
+  return open && mag > 0.0f ? ((__float_as_uint(mag) & ~15u) | (unsigned)(kTeam - 1 - t)) | 16u
+                            : (unsigned)(kTeam - 1 - t);
+}
+
 // LU of the team's real matrix, pivot order into pk[]
 template <typename T>
 __device__ inline bool team_lu_real(T* a, const T* a0, int t, unsigned mask, int* pk, int& step, T& inv) {
   step = kTeam;
 #pragma unroll
   for (int k = 0; k < kTeam; k++) {
-    double cand = step > k ? (double)fabs(a[k]) : -1.0;
-    int who = t;
-#pragma unroll
-    for (int o = kTeam / 2; o > 0; o >>= 1) {
-      const double oc = __shfl_xor_sync(mask, cand, o, kTeam);
-      const int ow = __shfl_xor_sync(mask, who, o, kTeam);
-      if (oc > cand || (oc == cand && ow < who)) {
-        cand = oc;
-        who = ow;
-      }
-    }
-    if (!(cand > 0.0)) return false;
+    const unsigned key = pivot_key(step > k, (float)fabs(a[k]), t);
+    const unsigned best = __reduce_max_sync(mask, key);
+    const int who = kTeam - 1 - (int)(best & 15u);
+    if ((best >> 4) == 0u) return false;  // no non-zero candidate
     if (t == 0) pk[k] = who;
     const T* prow = a0 + who * kRow;
     const T pinv = (T)1 / prow[k];
@@ -148,18 +149,10 @@ __device__ inline bool team_lu_cplx(T* ar, T* ai, const T* ar0, const T* ai0, in
   step = kTeam;
 #pragma unroll
   for (int k = 0; k < kTeam; k++) {
-    double cand = step > k ? (double)(fabs(ar[k]) + fabs(ai[k])) : -1.0;
-    int who = t;
-#pragma unroll
-    for (int o = kTeam / 2; o > 0; o >>= 1) {
-      const double oc = __shfl_xor_sync(mask, cand, o, kTeam);
-      const int ow = __shfl_xor_sync(mask, who, o, kTeam);
-      if (oc > cand || (oc == cand && ow < who)) {
-        cand = oc;
-        who = ow;
-      }
-    }
-    if (!(cand > 0.0)) return false;
+    const unsigned key = pivot_key(step > k, (float)(fabs(ar[k]) + fabs(ai[k])), t);
+    const unsigned best = __reduce_max_sync(mask, key);
+    const int who = kTeam - 1 - (int)(best & 15u);
+    if ((best >> 4) == 0u) return false;  // no non-zero candidate
     if (t == 0) pk[k] = who;
     const T* pr = ar0 + who * kRow;
     const T* pi = ai0 + who * kRow;
