@@ -151,19 +151,32 @@ mr_status mr_get_leaves(mr_ctx *ctx, uint64_t *keys, double *values, int64_t cap
 
 /* One grid adaptation (Sec. 3.1.2): projection, details d = u - P P u
  * (Eq. detail) against eps_j = 2^((d/2)(j-J)) eta, refinement of tagged
- * leaves, grading to the least graded tree, coarsening to a fixed point. */
+ * leaves, grading to the least graded tree, coarsening to a fixed point.
+ * eta = 0 on the uniform level-J grid is the identity (every node is tagged,
+ * nothing can be refined or coarsened) and returns at once.  MR_EINVAL for a
+ * negative or non-finite eta; MR_ESTATE if a detail is not finite (the state
+ * holds NaN or infinity); MR_ENOMEM if the adapted tree outgrows the leaf
+ * capacity given to mr_create (max_leaves). */
 mr_status mr_adapt(mr_ctx *ctx, double eta);
 
 /* Reaction sub-step R_dt (Sec. 2.1): every leaf integrates u' = f(u) over dt
  * with Radau5 (3-stage Radau IIA, simplified Newton, step-size control;
- * rtol, atol > 0). */
+ * rtol, atol > 0).  MR_EINVAL for dt <= 0 or tolerances <= 0; per-cell
+ * failures MR_ERADAU_HMIN (step size underflow), MR_ERADAU_MAXSTEPS (over
+ * 100000 attempts), MR_ERADAU_SINGULAR (five singular Newton matrices in a
+ * row), MR_ENONFINITE (a non-finite state); MR_ESTATE for a network model
+ * whose reactions are not set. */
 mr_status react_radau5(mr_ctx *ctx, double dt, double rtol, double atol);
 
 /* Diffusion sub-step D_dt (Sec. 2.1, Sec. 3.2.1): every species integrates
- * u' = D_i L u with the ROCK4-type stabilized method (tol > 0). */
+ * u' = D_i L u with the ROCK4-type stabilized method (tol > 0).  Species
+ * with D_i = 0 are left unchanged.  MR_EINVAL for dt <= 0 or tol <= 0;
+ * MR_EROCK_STEP if the step size collapses (below 1e-14 dt) or the step
+ * limit is reached; MR_ENONFINITE if the error norm is not finite. */
 mr_status diffuse_rock4(mr_ctx *ctx, double dt, double tol);
 
-/* One Strang step: mr_adapt(eta); R_{dt/2}; D_dt; R_{dt/2}. */
+/* One Strang step: mr_adapt(eta); R_{dt/2}; D_dt; R_{dt/2}.  Errors as for
+ * the three calls; the first failing phase ends the step. */
 mr_status strang_step(mr_ctx *ctx, double dt, double eta, double rtol, double atol,
                       double rock_tol);
 
