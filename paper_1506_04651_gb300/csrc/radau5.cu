@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
     if (cell < 0) {
       cell = atomicAdd(&dc->work_next, 1);
       if (cell >= N) break;
+      // finest leaves first: leaves are stored level-major, and the finest
+      // levels hold the front cells that need the most steps
+      cell = (int)(N - 1 - cell);
       if (B.inst) {
         int lo = 0, hi = B.n - 1;  // last instance with offs[b] <= cell
         while (lo < hi) {
