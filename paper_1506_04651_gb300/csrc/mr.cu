@@ -27,6 +27,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "mr_internal.cuh"
 
 namespace mrg {
@@ -510,41 +512,44 @@ __global__ void k_reg_table(const int32_t* __restrict__ irr_flag, const int32_t*
 // level is resolved.  What remains are leaves; the row is sorted by leaf index
 // (so the sweeps' sums are reproducible run to run) and written to a fixed
 // slot.  Weights are dyadic, so merging is exact in any order.
-template <int D>
-struct IrrCfg;
-template <>
-struct IrrCfg<2> {
+// Table sizes per warp.  3D rows are built first with a half-size table (more
+// resident warps); the few rows that do not fit (more than 512 cells or 320
+// leaves) are rebuilt by a second launch with the full-size table.
+struct IrrCfg2 {
   static constexpr int kCells = 256, kSort = kIrrSlot2, kWarps = 4;
 };
-template <>
-struct IrrCfg<3> {
+struct IrrCfg3 {
   static constexpr int kCells = 1024, kSort = kIrrSlot3, kWarps = 3;
 };
+struct IrrCfg3Small {
+  static constexpr int kCells = 512, kSort = 320, kWarps = 4;
+};
 
-static_assert(sizeof(int32_t) * IrrCfg<2>::kSort + sizeof(double) * IrrCfg<2>::kSort <=
-                  sizeof(unsigned long long) * IrrCfg<2>::kCells &&
-              sizeof(int32_t) * IrrCfg<3>::kSort + sizeof(double) * IrrCfg<3>::kSort <=
-                  sizeof(unsigned long long) * IrrCfg<3>::kCells,
+template <class Cfg>
+constexpr bool fits_in_keys() {
+  return sizeof(int32_t) * Cfg::kSort + sizeof(double) * Cfg::kSort <= sizeof(unsigned long long) * Cfg::kCells;
+}
+static_assert(fits_in_keys<IrrCfg2>() && fits_in_keys<IrrCfg3>() && fits_in_keys<IrrCfg3Small>(),
               "a row's leaves fit in the key bytes");
 
 constexpr unsigned long long kEmptyCell = ~0ull;
 constexpr int32_t kAbsent = -1, kInternal = -2, kUnresolved = -3;
 
-template <int D>
+template <int D, class Cfg>
 struct IrrShared {
   // the keys are dead once every cell is resolved, and the row's leaves are
   // collected into the same bytes for placement
   union {
-    unsigned long long key[IrrCfg<D>::kCells];  // (level << 48) | Morton code
+    unsigned long long key[Cfg::kCells];  // (level << 48) | Morton code
     struct {
-      int32_t skey[IrrCfg<D>::kSort];
-      double sval[IrrCfg<D>::kSort];
+      int32_t skey[Cfg::kSort];
+      double sval[Cfg::kSort];
     } row;
   };
-  double w[IrrCfg<D>::kCells];
-  int32_t st[IrrCfg<D>::kCells];  // leaf index, kAbsent or kInternal
-  int16_t order[IrrCfg<D>::kCells];  // table slots in the order the cells were named
-  int16_t list[IrrCfg<D>::kCells];   // slots of the cells one pass expands
+  double w[Cfg::kCells];
+  int32_t st[Cfg::kCells];  // leaf index, kAbsent or kInternal
+  int16_t order[Cfg::kCells];  // table slots in the order the cells were named
+  int16_t list[Cfg::kCells];   // slots of the cells one pass expands
   int n, cnt, lo, hi, bad;
 };
 
@@ -566,9 +571,9 @@ __global__ void k_status_map(const uint32_t* __restrict__ code, const uint8_t* _
 
 // name a cell: shared memory only; its status (leaf, internal, absent) is
 // looked up afterwards for all the cells a pass named at once (resolve)
-template <int D>
-__device__ inline void cell_add(IrrShared<D>& S, int j, const int* k, double w) {
-  constexpr int kC = IrrCfg<D>::kCells;
+template <int D, class Cfg>
+__device__ inline void cell_add(IrrShared<D, Cfg>& S, int j, const int* k, double w) {
+  constexpr int kC = Cfg::kCells;
   const uint32_t code = morton<D>(k);
   const unsigned long long key = ((unsigned long long)j << 48) | code;
   uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (kC - 1);
@@ -594,8 +599,8 @@ __device__ inline void cell_add(IrrShared<D>& S, int j, const int* k, double w) 
 
 // status of the cells named in order[from, to): one lane per cell, the
 // direct-map and leaf-index loads of all of them in flight together
-template <int D>
-__device__ inline void resolve(IrrShared<D>& S, const IrrMaps& M, const Level& L, int from, int to, int lane) {
+template <int D, class Cfg>
+__device__ inline void resolve(IrrShared<D, Cfg>& S, const IrrMaps& M, const Level& L, int from, int to, int lane) {
 #pragma unroll 4
   for (int e = from + lane; e < to; e += 32) {
     const int h = S.order[e];
@@ -605,16 +610,19 @@ __device__ inline void resolve(IrrShared<D>& S, const IrrMaps& M, const Level& L
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
-    k_irr_rows(const int32_t* __restrict__ irr_leaf, int64_t nrows, const int32_t* __restrict__ leaf_node,
-               const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
-               const int32_t* __restrict__ smap, Level L, int slot,
+// rowlist: the rows to build (null: all nrows); retry: where rows that do
+// not fit this table go (null: a row that does not fit its slot is an error)
+template <int D, class Cfg>
+__global__ void __launch_bounds__(32 * Cfg::kWarps, 2)
+    k_irr_rows(const int32_t* __restrict__ irr_leaf, int64_t nrows, const int32_t* __restrict__ rowlist,
+               const int32_t* __restrict__ leaf_node, const uint32_t* __restrict__ code,
+               const uint8_t* __restrict__ lvl, const int32_t* __restrict__ smap, Level L, int slot,
                int32_t* __restrict__ cnt, int32_t* __restrict__ col, double* __restrict__ wout,
-               float* __restrict__ wout_f, unsigned long long* rho_bits, DevCounters* dc) {
+               float* __restrict__ wout_f, unsigned long long* rho_bits, int32_t* __restrict__ retry,
+               DevCounters* dc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kC = IrrCfg<D>::kCells, kS = IrrCfg<D>::kSort;
-  IrrShared<D>& S = reinterpret_cast<IrrShared<D>*>(smem_raw)[threadIdx.x >> 5];
+  constexpr int kC = Cfg::kCells, kS = Cfg::kSort;
+  IrrShared<D, Cfg>& S = reinterpret_cast<IrrShared<D, Cfg>*>(smem_raw)[threadIdx.x >> 5];
   const IrrMaps M{smap};
   const int lane = threadIdx.x & 31;
   for (int q = lane; q < kC; q += 32) {
@@ -623,8 +631,9 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
   }
   if (lane == 0) S.n = 0;
   __syncwarp();
-  for (int64_t row = (int64_t)blockIdx.x * IrrCfg<D>::kWarps + (threadIdx.x >> 5); row < nrows;
-       row += (int64_t)gridDim.x * IrrCfg<D>::kWarps) {
+  for (int64_t item = (int64_t)blockIdx.x * Cfg::kWarps + (threadIdx.x >> 5); item < nrows;
+       item += (int64_t)gridDim.x * Cfg::kWarps) {
+    const int64_t row = rowlist ? rowlist[item] : item;
     if (lane == 0) {
       S.cnt = S.bad = 0;
       S.lo = 1 << 20;
@@ -645,8 +654,8 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
       q[a] += sg;
       if (q[a] >= 0 && q[a] < lim) {  // homogeneous Neumann: no flux through the boundary
         if (smap[L.doff[j] + morton<D>(q)] != kInternal) {
-          cell_add<D>(S, j, q, ih2);  // same-level leaf, or ghost by prediction
-          cell_add<D>(S, j, k, -ih2);
+          cell_add<D, Cfg>(S, j, q, ih2);  // same-level leaf, or ghost by prediction
+          cell_add<D, Cfg>(S, j, k, -ih2);
         } else {
           // finer side: minus the mean of the fluxes into the touching children
           for (int t = 0; t < (1 << D); t++) {
@@ -655,14 +664,14 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
             if (c[a] != 2 * q[a] + (sg > 0 ? 0 : 1)) continue;
             int g[3] = {c[0], c[1], c[2]};
             g[a] -= sg;
-            cell_add<D>(S, j + 1, g, -coef);
-            cell_add<D>(S, j + 1, c, coef);
+            cell_add<D, Cfg>(S, j + 1, g, -coef);
+            cell_add<D, Cfg>(S, j + 1, c, coef);
           }
         }
       }
     }
     __syncwarp();
-    resolve<D>(S, M, L, 0, S.n, lane);
+    resolve<D, Cfg>(S, M, L, 0, S.n, lane);
     __syncwarp();
     // gather the table slots of the cells at level jj with status st into
     // S.list (ballot compaction, every lane in step); returns their count
@@ -705,10 +714,10 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
           st[a] = mirror((c[a] >> 1) + off, jj - 1);
           w *= wpred(c[a] & 1, off);
         }
-        cell_add<D>(S, jj - 1, st, w);
+        cell_add<D, Cfg>(S, jj - 1, st, w);
       }
       __syncwarp();
-      resolve<D>(S, M, L, ne, S.n, lane);
+      resolve<D, Cfg>(S, M, L, ne, S.n, lane);
       __syncwarp();
     }
     // down: internal cells, coarsest level first, (cell, child) pairs over
@@ -727,10 +736,10 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
         const double w = S.w[h] * (1.0 / (1 << D));
         int ch[3] = {0, 0, 0};
         for (int a = 0; a < D; a++) ch[a] = 2 * c[a] + ((t >> a) & 1);
-        cell_add<D>(S, jj + 1, ch, w);
+        cell_add<D, Cfg>(S, jj + 1, ch, w);
       }
       __syncwarp();
-      resolve<D>(S, M, L, ne, S.n, lane);
+      resolve<D, Cfg>(S, M, L, ne, S.n, lane);
       __syncwarp();
     }
     // collect the leaves with non-zero weight, then sort them by leaf index
@@ -774,9 +783,14 @@ __global__ void __launch_bounds__(32 * IrrCfg<D>::kWarps, 2)
     for (int e = lane; e < ne; e += 32) S.w[S.order[e]] = 0.0;
     if (lane == 0) {
       cnt[row] = ok ? cntr : 0;
-      if (!ok) atomicExch(&dc->overflow, 1);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&dc->irr_nnz), (unsigned long long)cntr);
-      atomicMax(rho_bits, (unsigned long long)__double_as_longlong(sa));
+      if (ok) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&dc->irr_nnz), (unsigned long long)cntr);
+        atomicMax(rho_bits, (unsigned long long)__double_as_longlong(sa));
+      } else if (retry) {
+        retry[atomicAdd(&dc->nretry, 1)] = (int32_t)row;
+      } else {
+        atomicExch(&dc->overflow, 1);
+      }
       S.n = 0;
     }
     __syncwarp();
@@ -1069,23 +1083,30 @@ mr_status build_tables(mr_ctx* c) {
     MR_CUDA(c, cudaMemsetAsync(c->smap, 0xff, sizeof(int32_t) * c->cap_dense, c->stream));
     k_status_map<<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(t.code, t.lvl, t.node_leaf, L, t.nnodes, c->smap);
     c->launches++;
+    auto launch = [&](auto cfg, auto dim, const int32_t* rowlist, int64_t count, int32_t* retry) -> mr_status {
+      using Cfg = decltype(cfg);
+      constexpr int DD = decltype(dim)::value;
+      const size_t sm = sizeof(IrrShared<DD, Cfg>) * Cfg::kWarps;
+      MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<DD, Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      const int grid = (int)std::min<int64_t>((count + Cfg::kWarps - 1) / Cfg::kWarps, (int64_t)nsm * 16);
+      k_irr_rows<DD, Cfg><<<grid, 32 * Cfg::kWarps, sm, c->stream>>>(
+          c->irr_leaf, count, rowlist, t.leaf_node, t.code, t.lvl, c->smap, L, slot, c->irr_cnt, c->irr_col,
+          c->irr_w, c->irr_wf, c->rho_bits, retry, c->dc);
+      c->launches++;
+      MR_CUDA(c, cudaGetLastError());
+      return MR_OK;
+    };
     if (D == 2) {
-      const size_t sm = sizeof(IrrShared<2>) * IrrCfg<2>::kWarps;
-      MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      int grid = (int)std::min<int64_t>((nrows + IrrCfg<2>::kWarps - 1) / IrrCfg<2>::kWarps, (int64_t)nsm * 16);
-      k_irr_rows<2><<<grid, 32 * IrrCfg<2>::kWarps, sm, c->stream>>>(
-          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, c->smap, L, slot, c->irr_cnt, c->irr_col,
-          c->irr_w, c->irr_wf, c->rho_bits, c->dc);
+      MR_TRY(launch(IrrCfg2{}, std::integral_constant<int, 2>{}, nullptr, nrows, nullptr));
     } else {
-      const size_t sm = sizeof(IrrShared<3>) * IrrCfg<3>::kWarps;
-      MR_CUDA(c, cudaFuncSetAttribute(k_irr_rows<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      int grid = (int)std::min<int64_t>((nrows + IrrCfg<3>::kWarps - 1) / IrrCfg<3>::kWarps, (int64_t)nsm * 16);
-      k_irr_rows<3><<<grid, 32 * IrrCfg<3>::kWarps, sm, c->stream>>>(
-          c->irr_leaf, nrows, t.leaf_node, t.code, t.lvl, c->smap, L, slot, c->irr_cnt, c->irr_col,
-          c->irr_w, c->irr_wf, c->rho_bits, c->dc);
+      // half-size tables first, the rows that do not fit again with full-size ones
+      int32_t* retry = c->itmp;
+      MR_CUDA(c, cudaMemsetAsync(&c->dc->nretry, 0, sizeof(int), c->stream));
+      MR_TRY(launch(IrrCfg3Small{}, std::integral_constant<int, 3>{}, nullptr, nrows, retry));
+      MR_TRY(sync_counts(c));
+      if (c->hc.nretry > 0)
+        MR_TRY(launch(IrrCfg3{}, std::integral_constant<int, 3>{}, retry, c->hc.nretry, nullptr));
     }
-    c->launches++;
-    MR_CUDA(c, cudaGetLastError());
   }
   c->irr_slot = slot;
   MR_TRY(sync_counts(c));

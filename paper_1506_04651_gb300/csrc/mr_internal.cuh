@@ -102,6 +102,7 @@ struct DevCounters {
   int nleaves;
   int work_next;                // Radau5 work queue head
   int overflow;                 // irregular row exceeded its local capacity
+  int nretry;                   // rows left to the full-size row builder
 };
 
 // ---------------------------------------------------------------- context
