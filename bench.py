@@ -639,7 +639,10 @@ def run_batch(args, b):
                        "l2": "inputs larger than L2 (all instances' state and work vectors)"},
             "roofline": roof, "e2e": e2e, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
             "mixed": mixed, "kernels": {"joint_radau": {"ms": st["ms_react_kernel"], "launches": st["react_launches"],
-                                                       "tflops": ach}}}
+                                                       "tflops": ach},
+                                        "phases_ms_per_step": {"adapt_and_tables": st["ms_adapt_phase"] / args.steps,
+                                                               "react_joint": st["ms_react_kernel"] / args.steps,
+                                                               "diffuse": st["ms_diffuse_phase"] / args.steps}}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -191,19 +191,33 @@ mr_status strang_step(mr_ctx *ctx, double dt, double eta, double rtol, double at
  *                    / mr_get_leaves / mr_mass ... (owned by the batch; NULL
  *                    for a bad index).  Do not destroy it.
  *   mr_batch_run     nsteps Strang steps of every instance, eta[i] its
- *                    threshold: the adaptation and the diffusion of all
- *                    instances run concurrently on their streams, and each
- *                    reaction half step of all instances is one persistent
- *                    Radau5 launch over the union of their leaves (when all
- *                    instances use the BZ or all the NAGUMO model with one
- *                    precision; otherwise one launch per instance).  Every
- *                    cell is integrated with the same arithmetic as by
- *                    strang_step, so results equal stepping each context
- *                    alone.  Synchronises before returning; the first error
- *                    wins (per-instance detail in each context's last error).
- *   mr_batch_get_stats counters of the last mr_batch_run.  In the joint form
+ *                    threshold: the adaptation of all instances runs
+ *                    concurrently on their streams; each reaction half step
+ *                    of all instances is one persistent Radau5 launch over
+ *                    the union of their leaves (when all instances use the
+ *                    BZ or all the NAGUMO model with one precision; otherwise
+ *                    one launch per instance), and the diffusion sub-step of
+ *                    all instances is one persistent ROCK4 launch (when all
+ *                    are 2D with one or three species, the same species
+ *                    count and precision; otherwise one launch per instance,
+ *                    run concurrently).  Every cell is integrated with the
+ *                    same arithmetic as by strang_step, so reaction results
+ *                    equal stepping each context alone; in the joint
+ *                    diffusion each instance keeps its own step control, but
+ *                    its error norm is summed in another order, so its
+ *                    results agree with stepping it alone to rounding (and
+ *                    an accept / reject decision at the tolerance's edge may
+ *                    differ).  Synchronises before returning; the first
+ *                    error wins (per-instance detail in each context's last
+ *                    error).
+ *   mr_batch_diffuse the diffusion sub-step alone (diffuse_rock4 of every
+ *                    instance over dt with tolerance tol), joint or per
+ *                    instance as in mr_batch_run.  MR_EINVAL for dt <= 0 or
+ *                    not finite, or tol <= 0; synchronises before returning.
+ *   mr_batch_get_stats counters of the last mr_batch_run or mr_batch_diffuse.  In the joint form
  *                    the Radau5 counters are batch totals (the contexts' own
- *                    Radau5 counters are not updated).
+ *                    Radau5 counters are not updated); the ROCK4 counters of
+ *                    each context are its own in either form.
  */
 typedef struct mr_batch mr_batch;
 typedef struct {
@@ -214,13 +228,19 @@ typedef struct {
   int64_t react_launches;      /* joint Radau5 launches */
   int64_t radau_fev, radau_jac, radau_steps, radau_accept, radau_reject, radau_newton, radau_dec;
   double radau_alg_flops;      /* algorithmic FP64 operations of the joint launches */
-  int32_t joint_reaction, reserved;
+  int32_t joint_reaction;      /* 1: the reaction sub-steps ran as joint launches */
+  int32_t joint_diffusion;     /* 1: the diffusion sub-steps ran as joint launches */
+  double ms_adapt_phase, ms_diffuse_phase; /* host wall time of the adaptation and diffusion
+                                              phases over the run */
+  double ms_diffuse_kernel;    /* summed device time of the joint ROCK4 launches */
+  int64_t diffuse_launches;    /* joint ROCK4 launches */
 } mr_batch_stats;
 
 mr_status mr_batch_create(int n, const mr_problem *probs, int threads, mr_batch **out);
 mr_ctx *mr_batch_context(mr_batch *b, int i);
 mr_status mr_batch_run(mr_batch *b, int nsteps, double dt, const double *eta, double rtol, double atol,
                        double rock_tol);
+mr_status mr_batch_diffuse(mr_batch *b, double dt, double tol);
 mr_status mr_batch_get_stats(const mr_batch *b, mr_batch_stats *out);
 void mr_batch_destroy(mr_batch *b);
 

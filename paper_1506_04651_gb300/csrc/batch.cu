@@ -1,16 +1,19 @@
 // Batched serving: many independent instances (each its own grid, depth,
 // parameters and threshold) stepped together on one GPU.  Every instance
-// keeps its own context and CUDA stream; the grid adaptation and the
-// diffusion sub-step of all instances run concurrently, driven by a pool of
-// host threads (their phases synchronise with the host to size the trees),
-// and the two reaction sub-steps of every Strang step run as one persistent
-// Radau5 launch over the union of all instances' leaves, so that the stiff
-// cells of one instance overlap the cells at rest of the others and the
-// launch has one tail instead of one per instance.
+// keeps its own context and CUDA stream; the grid adaptation of all
+// instances runs concurrently, driven by a pool of host threads (its phases
+// synchronise with the host to size the trees).  The two reaction sub-steps
+// of every Strang step run as one persistent Radau5 launch over the union of
+// all instances' leaves, so that the stiff cells of one instance overlap the
+// cells at rest of the others and the launch has one tail instead of one per
+// instance; the diffusion sub-step runs as one persistent ROCK4 launch over
+// all instances (each with its own step control), so that the grid-wide
+// barriers of the stages are paid once for the batch, not once per instance.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <condition_variable>
 #include <functional>
@@ -92,6 +95,7 @@ struct mr_batch {
   cudaEvent_t ev_start = nullptr, ev_end = nullptr, ev_joint = nullptr;
   mrg::Pool* pool = nullptr;
   mrg::BatchReactScratch scratch;
+  mrg::BatchRockScratch rscratch;
   mr_batch_stats stats;
   const char* last_error = "";
 };
@@ -113,6 +117,7 @@ void batch_free(mr_batch* b) {
   if (b->ev_joint) cudaEventDestroy(b->ev_joint);
   if (b->stream) cudaStreamDestroy(b->stream);
   free_batch_scratch(b->scratch);
+  free_batch_rock(b->rscratch);
   delete b;
 }
 
@@ -173,6 +178,45 @@ mr_status react_all(mr_batch* b, double dt, double rtol, double atol) {
   return MR_OK;
 }
 
+// the diffusion sub-step: one joint launch when every instance is 2D with
+// one or three species, all alike in species count and precision, else
+// per instance (concurrently)
+mr_status diffuse_all(mr_batch* b, double dt, double tol) {
+  const mr_ctx* c0 = b->ctx[0];
+  bool joint = c0->d == 2 && (c0->m == 1 || c0->m == 3) && b->n * c0->m <= 512;
+  for (mr_ctx* c : b->ctx) joint = joint && c->d == 2 && c->m == c0->m && c->prob.precision == c0->prob.precision;
+  if (!joint) {
+    b->stats.joint_diffusion = 0;
+    return for_all(b, [&](int i) { return diffuse(b->ctx[i], dt, tol); });
+  }
+  for (int i = 0; i < b->n; i++) {
+    if (cudaEventRecord(b->ev[i], b->streams[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ev[i], 0) != cudaSuccess)
+      return MR_ECUDA;
+  }
+  double ms = 0.0;
+  const mr_status s = diffuse_batch(b->ctx.data(), b->n, dt, tol, b->stream, b->rscratch, &ms);
+  if (s) return s;
+  if (cudaEventRecord(b->ev_joint, b->stream) != cudaSuccess) return MR_ECUDA;
+  for (int i = 0; i < b->n; i++)
+    if (cudaStreamWaitEvent(b->streams[i], b->ev_joint, 0) != cudaSuccess) return MR_ECUDA;
+  b->stats.joint_diffusion = 1;
+  b->stats.ms_diffuse_kernel += ms;
+  b->stats.diffuse_launches++;
+  return MR_OK;
+}
+
+void reset_counters(mr_batch_stats& S) {
+  S.steps = 0;
+  S.leaf_updates = 0;
+  S.ms_react_kernel = 0.0;
+  S.react_launches = 0;
+  S.radau_fev = S.radau_jac = S.radau_steps = S.radau_accept = S.radau_reject = S.radau_newton = S.radau_dec = 0;
+  S.radau_alg_flops = 0.0;
+  S.ms_adapt_phase = S.ms_diffuse_phase = S.ms_diffuse_kernel = 0.0;
+  S.diffuse_launches = 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -227,12 +271,11 @@ mr_status mr_batch_run(mr_batch* b, int nsteps, double dt, const double* eta, do
   for (int i = 0; i < b->n; i++)
     if (!(eta[i] >= 0.0) || !isfinite(eta[i])) return MR_EINVAL;
   mr_batch_stats& S = b->stats;
-  S.steps = 0;
-  S.leaf_updates = 0;
-  S.ms_react_kernel = 0.0;
-  S.react_launches = 0;
-  S.radau_fev = S.radau_jac = S.radau_steps = S.radau_accept = S.radau_reject = S.radau_newton = S.radau_dec = 0;
-  S.radau_alg_flops = 0.0;
+  reset_counters(S);
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t0) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  };
   // device time from the start event (which every instance stream waits on)
   // to the end event (which waits on every instance stream)
   if (cudaEventRecord(b->ev_start, b->stream) != cudaSuccess) return MR_ECUDA;
@@ -240,15 +283,19 @@ mr_status mr_batch_run(mr_batch* b, int nsteps, double dt, const double* eta, do
     if (cudaStreamWaitEvent(b->streams[i], b->ev_start, 0) != cudaSuccess) return MR_ECUDA;
   mr_status s = MR_OK;
   for (int step = 0; step < nsteps && !s; step++) {
+    clk::time_point t0 = clk::now();
     s = for_all(b, [&](int i) {
       mr_status r = adapt(b->ctx[i], eta[i]);
       return r ? r : build_tables(b->ctx[i]);
     });
+    S.ms_adapt_phase += ms_since(t0);
     if (s) break;
     for (mr_ctx* c : b->ctx) S.leaf_updates += c->tb[c->cur].nleaves;
     s = react_all(b, 0.5 * dt, rtol, atol);
     if (s) break;
-    s = for_all(b, [&](int i) { return diffuse(b->ctx[i], dt, rock_tol); });
+    t0 = clk::now();
+    s = diffuse_all(b, dt, rock_tol);
+    S.ms_diffuse_phase += ms_since(t0);
     if (s) break;
     s = react_all(b, 0.5 * dt, rtol, atol);
     S.steps++;
@@ -263,6 +310,30 @@ mr_status mr_batch_run(mr_batch* b, int nsteps, double dt, const double* eta, do
   cudaEventElapsedTime(&ms, b->ev_start, b->ev_end);
   S.ms_device = ms;
   if (s) b->last_error = "a batched step failed (see the instance contexts' last errors)";
+  return s;
+}
+
+mr_status mr_batch_diffuse(mr_batch* b, double dt, double tol) {
+  if (!b || !(dt > 0.0) || !isfinite(dt) || !(tol > 0.0)) return MR_EINVAL;
+  reset_counters(b->stats);
+  if (cudaEventRecord(b->ev_start, b->stream) != cudaSuccess) return MR_ECUDA;
+  for (int i = 0; i < b->n; i++)
+    if (cudaStreamWaitEvent(b->streams[i], b->ev_start, 0) != cudaSuccess) return MR_ECUDA;
+  mr_status s = for_all(b, [&](int i) { return build_tables(b->ctx[i]); });
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!s) s = diffuse_all(b, dt, tol);
+  b->stats.ms_diffuse_phase =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < b->n; i++) {
+    cudaEventRecord(b->ev[i], b->streams[i]);
+    cudaStreamWaitEvent(b->stream, b->ev[i], 0);
+  }
+  cudaEventRecord(b->ev_end, b->stream);
+  if (cudaEventSynchronize(b->ev_end) != cudaSuccess && !s) s = MR_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->ev_start, b->ev_end);
+  b->stats.ms_device = ms;
+  if (s) b->last_error = "a batched diffusion failed (see the instance contexts' last errors)";
   return s;
 }
 

@@ -117,7 +117,7 @@ void free_all(mr_ctx* c) {
   cudaFree(c->V); cudaFree(c->Vnew); cudaFree(c->fl_state); cudaFree(c->fl_forced);
   cudaFree(c->fl_final); cudaFree(c->grank); cudaFree(c->tag); cudaFree(c->smap); cudaFree(c->scan_tmp);
   cudaFree(c->itmp); cudaFree(c->nbr); cudaFree(c->leaf_lvl); cudaFree(c->irr_leaf); cudaFree(c->reg_tab);
-  cudaFree(c->irr_cnt); cudaFree(c->irr_ptr); cudaFree(c->irr_col); cudaFree(c->irr_w); cudaFree(c->irr_wf);
+  cudaFree(c->irr_cnt); cudaFree(c->irr_ptr); cudaFree(c->irr_col); cudaFree(c->irr_w); cudaFree(c->irr_wf); cudaFree(c->e2buf);
   for (int q = 0; q < 6; q++) cudaFree(c->work[q]);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->complexity); cudaFree(c->dc);
   cudaFree(c->rho_bits);

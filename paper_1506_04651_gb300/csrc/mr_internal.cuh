@@ -156,6 +156,7 @@ struct mr_ctx {
   int32_t* irr_col = nullptr;
   double* irr_w = nullptr;
   float* irr_wf = nullptr;           // the merged-row weights in FP32 (exact, dyadic)
+  double* e2buf = nullptr;           // [m][cap_leaves] per-leaf error terms of the joint diffusion (lazy)
   int64_t irr_cap = 0;
   int irr_slot = 0;                  // row stride of irr_col / irr_w
   double* rock_tab = nullptr;        // ROCK4-type coefficients of every stage count
@@ -244,5 +245,22 @@ void free_batch_scratch(BatchReactScratch& S);
 int rock4_coeffs(int s, double* mu, double* nu, double* kap, double* w, double* errc);
 double rock4_ell(int s);
 mr_status diffuse(mr_ctx* c, double dt, double tol);
+
+// Diffusion sub-step of several 2D contexts (same species count, one or three,
+// and precision) as one cooperative launch; the caller owns the scratch.
+struct BatchRockScratch {
+  void* inst = nullptr;
+  int64_t* off = nullptr;
+  void* ctl = nullptr;
+  int* ptr = nullptr;
+  double* part = nullptr;
+  int* flags = nullptr;
+  int cap = 0;
+  int64_t part_cap = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStream_t stream, BatchRockScratch& S,
+                        double* kernel_ms);
+void free_batch_rock(BatchRockScratch& S);
 
 }  // namespace mrg

@@ -181,20 +181,21 @@ __device__ inline double ell_dev(int s) { return 0.336 * (double)s * s - 2.7; }
 
 // choose the next step of every species (one thread per block, on the
 // block's copy of the control)
-__device__ void rock_prepare(const PersArgs& P, RockCtl& C, int64_t N, double leafb) {
+__device__ void rock_prepare(int m, double dt, const double* Dc, double rho_L, RockCtl& C, int64_t N,
+                             double leafb) {
   int nmax = 0, any = 0;
   double bytes = 0.0;
-  for (int i = 0; i < P.m; i++) {
+  for (int i = 0; i < m; i++) {
     if (C.done[i]) continue;
-    if (C.h[i] <= 1e-14 * P.dt) {
+    if (C.h[i] <= 1e-14 * dt) {
       C.status = MR_EROCK_STEP;
       C.finished = 1;
       return;
     }
-    const double rho = P.Dc[i] * P.rho;
+    const double rho = Dc[i] * rho_L;
     C.last[i] = 0;
-    if (C.t[i] + 1.0001 * C.h[i] >= P.dt) {
-      C.h[i] = P.dt - C.t[i];
+    if (C.t[i] + 1.0001 * C.h[i] >= dt) {
+      C.h[i] = dt - C.t[i];
       C.last[i] = 1;
     }
     int s = kSmax;
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     }
   };
   __syncthreads();
-  if (threadIdx.x == 0) rock_prepare(P, C, N, leafb);
+  if (threadIdx.x == 0) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, leafb);
   __syncthreads();
   if constexpr (!kF64) {
     // the mixed form integrates a float copy of the state
@@ -563,7 +564,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
         C.h[i] *= fac;
       }
       C.rounds++;
-      if (!C.finished) rock_prepare(P, C, N, leafb);
+      if (!C.finished) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, leafb);
     }
     __syncthreads();
   }
@@ -577,6 +578,493 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     for (int64_t r = tid; r < N; r += nth) u[r] = (double)y[r];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.ctl = C;
+}
+
+// ------------------------------------------------------------ joint driver (batches)
+// One cooperative launch integrates the diffusion sub-step of every instance
+// of a batch (2D, same species count and precision).  Every (instance,
+// species) pair keeps its own step control, stage count and buffers, as in
+// the one-instance driver; block 0 takes the control of all pairs and
+// publishes it through global memory (one more grid barrier per step).  Each
+// sweep runs over the concatenated tables of the instances that still have a
+// pair in that sweep (compacted per sweep, so instances that finished early,
+// or whose stage count is lower, cost nothing), and each error norm is summed
+// from per-leaf terms in fixed chunks, so results do not depend on the
+// schedule.
+constexpr int kChunk = 8192;  // leaves per partial sum of an error norm
+
+struct JInst {
+  double* U;
+  double* W[6];
+  double* E2;  // [m][capL]: per leaf and species, the squared scaled error of the step
+  const int4* reg;
+  const int32_t* irr_leaf;
+  const int32_t* cnt;
+  const int32_t* col;
+  const double* w;
+  const float* wf;
+  int64_t N, capL, nreg, nirr;
+  int slot;
+  double rho;
+  double Dc[kMaxM];
+};
+
+struct JArgs {
+  const JInst* inst;
+  int n, m;
+  const int64_t* off;  // [4][n + 1] prefix offsets: regular leaves, merged rows, leaves, error chunks
+  double dt, tol;
+  RockCtl* ctl;  // [n]
+  int* ptr;      // [n * kMaxM][5]: pool index of the state, of the three recurrence buffers, L y slot
+  double* part;  // [chunks][kMaxM]: chunk sums of the squared scaled errors
+  int* flags;    // [0] every instance finished, [1] largest recurrence stage count
+  RockTab tab;
+};
+
+// a pair's control as read at the start of a round
+struct PairCtl {
+  double h;
+  int s, n, a, on;  // on: the pair steps in this round
+  int py, pr[3], ly;
+};
+
+// last k in [0, cnt) with off[k] <= q
+__device__ inline int bisect(const int64_t* off, int cnt, int64_t q) {
+  int lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= q)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int M, typename VT>
+__global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
+  constexpr bool kF64 = std::is_same<VT, double>::value;
+  constexpr int D = 2, G = 2;
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char jsm[];
+  const int n = A.n, L = n * M;
+  Ops<VT>* s_ops = reinterpret_cast<Ops<VT>*>(jsm);
+  PairCtl* s_pc = reinterpret_cast<PairCtl*>(s_ops + L);
+  int64_t* s_off = reinterpret_cast<int64_t*>(s_pc + L);  // [4][n + 1] as A.off
+  int64_t* s_coff = s_off + 4 * (n + 1);                    // [3][n + 1] the same over the active instances
+  int* s_cmap = reinterpret_cast<int*>(s_coff + 3 * (n + 1));  // the active instances
+  int* s_act = s_cmap + n;                                     // [L]
+  __shared__ double sh[kBlock];
+  __shared__ int s_nact;
+  for (int q = threadIdx.x; q < 4 * (n + 1); q += blockDim.x) s_off[q] = A.off[q];
+  __syncthreads();
+  const int64_t* reg_off = s_off;
+  const int64_t* irr_off = s_off + (n + 1);
+  const int64_t* leaf_off = s_off + 2 * (n + 1);
+  const int64_t* chk_off = s_off + 3 * (n + 1);
+  const int64_t* creg = s_coff;
+  const int64_t* cirr = s_coff + (n + 1);
+  const int64_t* cleaf = s_coff + 2 * (n + 1);
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+  // a thread's indices increase: its cursor is found once by bisection,
+  // then walks forward
+  auto seek = [&](const int64_t* off, int cnt, int64_t q, int& k) {
+    if (k < 0)
+      k = bisect(off, cnt, q);
+    else
+      while (off[k + 1] <= q) k++;
+  };
+
+  auto fvec = [&](const JInst& I, int q, int sp) -> VT* {
+    return reinterpret_cast<VT*>(reinterpret_cast<float*>(I.W[q >> 1]) + (q & 1) * (int64_t)A.m * I.capL) +
+           (int64_t)sp * I.capL;
+  };
+  auto pool = [&](const JInst& I, int sp, int k) -> VT* {
+    if constexpr (kF64)
+      return reinterpret_cast<VT*>(k == 0 ? I.U : I.W[k - 1]) + (int64_t)sp * I.capL;
+    else
+      return fvec(I, k, sp);
+  };
+  auto Wp = [&](const JInst& I, int sp, int q) -> VT* {  // q = 3 accumulator, 4 / 5 L y
+    if constexpr (kF64)
+      return reinterpret_cast<VT*>(I.W[q]) + (int64_t)sp * I.capL;
+    else
+      return fvec(I, q + 1, sp);
+  };
+  // the published control of every pair, once per round
+  auto load_ctl = [&]() {
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+      const int i = l / M, sp = l % M;
+      PairCtl p;
+      p.on = 0;
+      if (sp < A.m) {
+        const RockCtl& C = A.ctl[i];
+        p.on = !__ldcg(&C.done[sp]) && !__ldcg(&C.finished);
+        if (p.on) {
+          const int* pt = A.ptr + 5 * (i * kMaxM + sp);
+          p.h = __ldcg(&C.h[sp]);
+          p.s = __ldcg(&C.s[sp]);
+          p.n = __ldcg(&C.n[sp]);
+          p.a = __ldcg(&C.a[sp]);
+          p.py = __ldcg(pt);
+          p.pr[0] = __ldcg(pt + 1);
+          p.pr[1] = __ldcg(pt + 2);
+          p.pr[2] = __ldcg(pt + 3);
+          p.ly = __ldcg(pt + 4);
+        }
+      }
+      s_pc[l] = p;
+    }
+    __syncthreads();
+  };
+  // operands of pair l = (instance, species) in `phase`; false if it sits out
+  auto ops_for = [&](int phase, int l, Ops<VT>& o) -> bool {
+    const PairCtl& p = s_pc[l];
+    if (!p.on) return false;
+    const int i = l / M, sp = l % M;
+    const JInst& I = A.inst[i];
+    const double* tb = A.tab.data + A.tab.off[p.s];
+    const double hd = p.h * I.Dc[sp];
+    const int nn = p.n;
+    VT* Y = pool(I, sp, p.py);
+    auto Rb = [&](int q) { return pool(I, sp, p.pr[q]); };
+    o.b = nullptr;
+    o.acc = nullptr;
+    o.lx = nullptr;
+    o.yn = Y;
+    if (phase < kPhaseFinish) {  // stage j >= 2
+      const int j = phase;
+      if (j > nn) return false;
+      o.kind = K_STAGE;
+      o.x = Rb((j - 2) % 3);
+      o.a = o.x;
+      o.b = j == 2 ? Y : Rb((j - 3) % 3);
+      o.out = Rb((j - 1) % 3);
+      o.ca = (VT)tb[10 + (j - 1)];
+      o.cb = (VT)tb[10 + nn + (j - 1)];
+      o.cl = (VT)(tb[10 + 2 * nn + (j - 1)] * hd);
+      return true;
+    }
+    const double* w = tb + 1;
+    const double* e = tb + 6;
+    const int a = p.a, b = (a + 1) % 3, cc = (a + 2) % 3;
+    o.kind = phase - kPhaseFinish;
+    switch (o.kind) {
+      case K_STAGE1:
+        o.x = Y; o.a = Y; o.out = Rb(0); o.lx = Wp(I, sp, 4 + p.ly);
+        o.ca = (VT)tb[10]; o.cl = (VT)(tb[10 + 2 * nn] * hd);
+        break;
+      case K_H3: o.x = Rb(a); o.a = Rb(a); o.out = Rb(b); o.ca = (VT)w[3]; o.cl = (VT)(w[4] * hd); break;
+      case K_H2: o.x = Rb(b); o.a = Rb(a); o.out = Rb(cc); o.ca = (VT)w[2]; o.cl = (VT)hd; break;
+      case K_H1:
+        o.x = Rb(cc); o.a = Rb(a); o.out = Rb(b); o.acc = Wp(I, sp, 3); o.ca = (VT)w[1]; o.cl = (VT)hd;
+        o.e0 = (VT)e[0]; o.e1 = (VT)e[1]; o.e2 = (VT)e[2];
+        break;
+      case K_H0: o.x = Rb(b); o.a = Rb(a); o.out = Rb(cc); o.acc = Wp(I, sp, 3); o.ca = (VT)1; o.cl = (VT)hd; break;
+      default:
+        o.x = Rb(cc); o.a = nullptr; o.out = nullptr; o.acc = Wp(I, sp, 3); o.lx = Wp(I, sp, 5 - p.ly);
+        o.cl = (VT)(e[3] * hd);
+    }
+    return true;
+  };
+  // operands of every pair in `phase`, then the instances with an active
+  // pair compacted (warp 0: ballot for the positions, shuffle scans for the
+  // offsets)
+  auto build_ops = [&](int phase) {
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) s_act[l] = ops_for(phase, l, s_ops[l]);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int cnt = 0;
+      int64_t c0 = 0, c1 = 0, c2 = 0;
+      if (lane == 0) s_coff[0] = s_coff[n + 1] = s_coff[2 * (n + 1)] = 0;
+      for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        bool on = false;
+        if (i < n)
+#pragma unroll
+          for (int sp = 0; sp < M; sp++) on = on || s_act[i * M + sp];
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        int64_t v0 = on ? reg_off[i + 1] - reg_off[i] : 0;
+        int64_t v1 = on ? irr_off[i + 1] - irr_off[i] : 0;
+        int64_t v2 = on ? leaf_off[i + 1] - leaf_off[i] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int64_t t0 = __shfl_up_sync(0xffffffffu, v0, d), t1 = __shfl_up_sync(0xffffffffu, v1, d),
+                        t2 = __shfl_up_sync(0xffffffffu, v2, d);
+          if (lane >= d) {
+            v0 += t0;
+            v1 += t1;
+            v2 += t2;
+          }
+        }
+        if (on) {
+          const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+          s_cmap[pos] = i;
+          s_coff[pos + 1] = c0 + v0;
+          s_coff[(n + 1) + pos + 1] = c1 + v1;
+          s_coff[2 * (n + 1) + pos + 1] = c2 + v2;
+        }
+        cnt += __popc(bal);
+        c0 += __shfl_sync(0xffffffffu, v0, 31);
+        c1 += __shfl_sync(0xffffffffu, v1, 31);
+        c2 += __shfl_sync(0xffffffffu, v2, 31);
+      }
+      if (lane == 0) s_nact = cnt;
+    }
+    __syncthreads();
+  };
+  // the embedded estimate of one leaf: its squared scaled error goes to E2
+  auto finish = [&](const Ops<VT>& o, const JInst& I, int sp, int64_t r, VT Lx) {
+    if (o.kind == K_FSAL) {
+      o.lx[r] = Lx;
+      const double ee = (double)(o.acc[r] + o.cl * Lx);
+      const double sc = A.tol + A.tol * fmax(fabs((double)o.yn[r]), fabs((double)o.x[r]));
+      I.E2[(int64_t)sp * I.capL + r] = (ee / sc) * (ee / sc);
+    } else {
+      double unused = 0.0;
+      combine<VT>(o, r, Lx, A.tol, unused);
+    }
+  };
+  // one operator sweep over the active instances: regular leaves one thread
+  // each, merged rows G lanes each (taken from the last threads)
+  auto sweep = [&]() {
+    const int na = s_nact;
+    const int64_t nreg = creg[na], nirr = cirr[na];
+    int k = -1;
+    for (int64_t q = tid; q < nreg; q += nth) {
+      seek(creg, na, q, k);
+      const int i = s_cmap[k];
+      const JInst& I = A.inst[i];
+      const int64_t ql = q - creg[k];
+      const int4 e0 = I.reg[2 * ql], e1 = I.reg[2 * ql + 1];
+      const int v[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+      const int64_t r = v[0];
+      VT ih2;
+      if constexpr (kF64)
+        ih2 = c_ih2[v[1 + 2 * D]];
+      else
+        ih2 = c_ih2f[v[1 + 2 * D]];
+#pragma unroll
+      for (int sp = 0; sp < M; sp++) {
+        const int l = i * M + sp;
+        if (!s_act[l]) continue;
+        const Ops<VT>& o = s_ops[l];
+        const VT* x = o.x;
+        VT sx = x[v[1]];
+#pragma unroll
+        for (int f = 1; f < 2 * D; f++) sx += x[v[1 + f]];
+        finish(o, I, sp, r, (sx - (VT)(2 * D) * x[r]) * ih2);
+      }
+    }
+    const int64_t grp = (nth - 1 - tid) / G, ngrp = nth / G;
+    const int64_t rounds = (nirr + ngrp - 1) / ngrp;
+    k = -1;
+    for (int64_t kk = 0; kk < rounds; kk++) {
+      const int64_t row = grp + kk * ngrp;
+      const bool have = row < nirr;
+      int i = 0;
+      VT vs[M];
+#pragma unroll
+      for (int sp = 0; sp < M; sp++) vs[sp] = (VT)0;
+      int32_t r = 0;
+      if (have) {
+        seek(cirr, na, row, k);
+        i = s_cmap[k];
+        const JInst& I = A.inst[i];
+        const int64_t rl = row - cirr[k];
+        r = I.irr_leaf[rl];
+        const int cnt = I.cnt[rl];
+        const int32_t* col = I.col + rl * (int64_t)I.slot;
+        const VT* wr;
+        if constexpr (kF64)
+          wr = I.w + rl * (int64_t)I.slot;
+        else
+          wr = I.wf + rl * (int64_t)I.slot;
+#pragma unroll 4
+        for (int e = sub; e < cnt; e += G) {
+          const int32_t cidx = col[e];
+          const VT we = wr[e];
+#pragma unroll
+          for (int sp = 0; sp < M; sp++)
+            if (s_act[i * M + sp]) vs[sp] += we * s_ops[i * M + sp].x[cidx];
+        }
+      }
+#pragma unroll
+      for (int sp = 0; sp < M; sp++)
+        for (int sft = G / 2; sft > 0; sft >>= 1) vs[sp] += __shfl_xor_sync(0xffffffffu, vs[sp], sft);
+      if (have && sub == 0) {
+        const JInst& I = A.inst[i];
+#pragma unroll
+        for (int sp = 0; sp < M; sp++)
+          if (s_act[i * M + sp]) finish(s_ops[i * M + sp], I, sp, r, vs[sp]);
+      }
+    }
+  };
+  // accept / reject and the next step of instance i (one thread of block 0)
+  auto control = [&](int i) {
+    RockCtl& C = A.ctl[i];
+    const JInst& I = A.inst[i];
+    for (int sp = 0; sp < A.m; sp++) {
+      C.acc_prev[sp] = 0;
+      if (C.done[sp]) continue;
+      double e2 = 0.0;
+      for (int64_t c = chk_off[i]; c < chk_off[i + 1]; c++) e2 += __ldcg(&A.part[c * kMaxM + sp]);
+      const double err = sqrt(e2 / (double)I.N);
+      C.err[sp] = err;
+      if (!isfinite(err)) {
+        C.status = MR_ENONFINITE;
+        C.finished = 1;
+        break;
+      }
+      const double fac = err == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.8 * pow(err, -0.25)));
+      if (err <= 1.0) {
+        // the candidate y_{n+1} (recurrence buffer (a+2) % 3) becomes the state
+        int* pt = A.ptr + 5 * (i * kMaxM + sp);
+        const int cp = (C.a[sp] + 2) % 3;
+        const int t = pt[0];
+        pt[0] = pt[1 + cp];
+        pt[1 + cp] = t;
+        pt[4] ^= 1;
+        C.acc_prev[sp] = 1;
+        C.c_prev[sp] = cp;
+        C.t[sp] = C.last[sp] ? A.dt : C.t[sp] + C.h[sp];
+        if (C.last[sp]) C.done[sp] = 1;
+      } else {
+        C.rejects++;
+      }
+      C.h[sp] *= fac;
+    }
+    C.rounds++;
+    if (!C.finished) rock_prepare(A.m, A.dt, I.Dc, I.rho, C, I.N, I.N * (8.0 * D + 1.0));
+  };
+  auto publish = [&]() {  // block 0: the flags every block reads after the next barrier
+    if (blockIdx.x == 0) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int fin = 1, nmax = 0;
+        for (int i = 0; i < n; i++) {
+          const bool f = A.ctl[i].finished || A.ctl[i].status;
+          fin = fin && f;
+          if (!f) nmax = max(nmax, A.ctl[i].nmax);
+        }
+        A.flags[0] = fin;
+        A.flags[1] = nmax;
+      }
+      __threadfence();
+    }
+  };
+
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const JInst& I = A.inst[i];
+      rock_prepare(A.m, A.dt, I.Dc, I.rho, A.ctl[i], I.N, I.N * (8.0 * D + 1.0));
+      for (int sp = 0; sp < kMaxM; sp++) {
+        int* pt = A.ptr + 5 * (i * kMaxM + sp);
+        pt[0] = 0;
+        pt[1] = 1;
+        pt[2] = 2;
+        pt[3] = 3;
+        pt[4] = 0;
+      }
+    }
+  }
+  publish();
+  const int64_t nleaf_all = leaf_off[n];
+  if constexpr (!kF64) {  // the mixed form integrates a float copy of the state
+    int k = -1;
+    for (int64_t q = tid; q < nleaf_all; q += nth) {
+      seek(leaf_off, n, q, k);
+      const JInst& I = A.inst[k];
+      const int64_t r = q - leaf_off[k];
+      for (int sp = 0; sp < A.m; sp++) pool(I, sp, 0)[r] = (VT)I.U[(int64_t)sp * I.capL + r];
+    }
+  }
+  grid.sync();
+  bool first = true;
+  for (int round = 0; round < 20000; round++) {
+    if (__ldcg(&A.flags[0])) break;
+    const int nmax = __ldcg(&A.flags[1]);
+    load_ctl();
+    // stage 1: P_1 = y + kap_1 h L y (an operator sweep in the first step,
+    // then an axpy on the kept L y)
+    build_ops(kPhaseFinish + K_STAGE1);
+    if (first) {
+      sweep();
+    } else {
+      const int na = s_nact;
+      const int64_t nl = cleaf[na];
+      int k = -1;
+      for (int64_t q = tid; q < nl; q += nth) {
+        seek(cleaf, na, q, k);
+        const int i = s_cmap[k];
+        const int64_t r = q - cleaf[k];
+#pragma unroll
+        for (int sp = 0; sp < M; sp++) {
+          const int l = i * M + sp;
+          if (!s_act[l]) continue;
+          const Ops<VT>& o = s_ops[l];
+          o.out[r] = o.ca * o.a[r] + o.cl * o.lx[r];
+        }
+      }
+    }
+    first = false;
+    grid.sync();
+    for (int j = 2; j <= nmax; j++) {  // recurrence stages P_j -> R[(j-1) % 3]
+      build_ops(j);
+      sweep();
+      grid.sync();
+    }
+    for (int mode = K_H3; mode <= K_FSAL; mode++) {  // finishing procedure, embedded estimate
+      build_ops(kPhaseFinish + mode);
+      sweep();
+      grid.sync();
+    }
+    // chunk sums of the error terms (the pairs of the last sweep), one block
+    // per chunk in a fixed order
+    for (int64_t c = blockIdx.x; c < chk_off[n]; c += gridDim.x) {
+      const int i = bisect(chk_off, n, c);
+      const JInst& I = A.inst[i];
+      const int64_t r0 = (c - chk_off[i]) * kChunk, r1 = min(I.N, r0 + kChunk);
+      for (int sp = 0; sp < M; sp++) {
+        if (!s_act[i * M + sp]) continue;
+        double v = 0.0;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) v += __ldcg(&I.E2[(int64_t)sp * I.capL + r]);
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int w = kBlock / 2; w > 0; w >>= 1) {
+          if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+          __syncthreads();
+        }
+        if (threadIdx.x == 0) A.part[c * kMaxM + sp] = sh[0];
+        __syncthreads();
+      }
+    }
+    grid.sync();
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (!A.ctl[i].finished) control(i);
+    publish();
+    grid.sync();
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (!A.ctl[i].finished) A.ctl[i].status = MR_EROCK_STEP;
+  // the final states back into the state arrays where a swap moved them
+  // (FP64), or converted back (FP32)
+  int k = -1;
+  for (int64_t q = tid; q < nleaf_all; q += nth) {
+    seek(leaf_off, n, q, k);
+    const JInst& I = A.inst[k];
+    const int64_t r = q - leaf_off[k];
+    for (int sp = 0; sp < A.m; sp++) {
+      const int py = __ldcg(A.ptr + 5 * (k * kMaxM + sp));
+      if (kF64 && py == 0) continue;
+      I.U[(int64_t)sp * I.capL + r] = (double)pool(I, sp, py)[r];
+    }
+  }
 }
 
 // ------------------------------------------------------------ host coefficients
@@ -948,12 +1436,155 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   S.rock_smax = hctl.smax;
   S.rock_kernel_ms += ms;
   S.rock_kernel_launches++;
-  S.rock_alg_bytes += hctl.bytes + 12.0 * S.irregular_nnz * 0.0;
+  S.rock_alg_bytes += hctl.bytes;
   if (hctl.status) {
     c->last_error = "ROCK4 step control failed";
     return (mr_status)hctl.status;
   }
   return MR_OK;
+}
+
+
+// ------------------------------------------------------------ joint driver (host)
+namespace {
+template <int M, typename VT>
+const void* joint_kernel() {
+  return (const void*)k_rock_joint<M, VT>;
+}
+}  // namespace
+
+void free_batch_rock(BatchRockScratch& S) {
+  cudaFree(S.inst);
+  cudaFree(S.off);
+  cudaFree(S.ctl);
+  cudaFree(S.ptr);
+  cudaFree(S.part);
+  cudaFree(S.flags);
+  for (int q = 0; q < 2; q++)
+    if (S.ev[q]) cudaEventDestroy(S.ev[q]);
+  S = BatchRockScratch{};
+}
+
+mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStream_t stream, BatchRockScratch& S,
+                        double* kernel_ms) {
+  if (n < 1) return MR_EINVAL;
+  const int m = cs[0]->m, prec = cs[0]->prob.precision;
+  if (cs[0]->d != 2 || (m != 1 && m != 3)) return MR_EINVAL;
+  for (int b = 1; b < n; b++)
+    if (cs[b]->d != 2 || cs[b]->m != m || cs[b]->prob.precision != prec) return MR_EINVAL;
+  for (int b = 0; b < n; b++) {
+    MR_TRY(build_tables(cs[b]));
+    MR_TRY(init_ih2(cs[b]));
+    if (!cs[b]->e2buf) MR_CUDA(cs[b], cudaMalloc(&cs[b]->e2buf, sizeof(double) * (size_t)m * cs[b]->cap_leaves));
+  }
+  JArgs A;
+  memset(&A, 0, sizeof A);
+  if (!device_table(cs[0], &A.tab)) return MR_ESTATE;
+  std::vector<JInst> hin(n);
+  std::vector<int64_t> off(4 * (n + 1), 0);
+  std::vector<RockCtl> hctl(n);
+  for (int b = 0; b < n; b++) {
+    mr_ctx* c = cs[b];
+    JInst& I = hin[b];
+    memset(&I, 0, sizeof I);
+    I.U = c->tb[c->cur].U;
+    for (int q = 0; q < 6; q++) I.W[q] = c->work[q];
+    I.E2 = c->e2buf;
+    I.reg = c->reg_tab;
+    I.irr_leaf = c->irr_leaf;
+    I.cnt = c->irr_cnt;
+    I.col = c->irr_col;
+    I.w = c->irr_w;
+    I.wf = c->irr_wf;
+    I.N = c->tb[c->cur].nleaves;
+    I.capL = c->cap_leaves;
+    I.nirr = c->stats.irregular_rows;
+    I.nreg = I.N - I.nirr;
+    I.slot = c->irr_slot;
+    I.rho = c->rho;
+    for (int i = 0; i < m; i++) I.Dc[i] = c->prob.D[i];
+    off[b + 1] = off[b] + I.nreg;
+    off[(n + 1) + b + 1] = off[(n + 1) + b] + I.nirr;
+    off[2 * (n + 1) + b + 1] = off[2 * (n + 1) + b] + I.N;
+    off[3 * (n + 1) + b + 1] = off[3 * (n + 1) + b] + (I.N + kChunk - 1) / kChunk;
+    RockCtl& C = hctl[b];
+    memset(&C, 0, sizeof C);
+    for (int i = 0; i < kMaxM; i++) {
+      C.h[i] = dt;
+      C.done[i] = i >= m || !(dt > 0.0) || c->prob.D[i] == 0.0 || I.N == 0;
+    }
+  }
+  const int64_t chunks = std::max<int64_t>(1, off[4 * (n + 1) - 1]);
+  if (S.cap < n || S.part_cap < chunks) {
+    free_batch_rock(S);
+    if (cudaMalloc(&S.inst, sizeof(JInst) * n) != cudaSuccess ||
+        cudaMalloc(&S.off, sizeof(int64_t) * 4 * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&S.ctl, sizeof(RockCtl) * n) != cudaSuccess ||
+        cudaMalloc(&S.ptr, sizeof(int) * 5 * kMaxM * n) != cudaSuccess ||
+        cudaMalloc(&S.part, sizeof(double) * kMaxM * 2 * chunks) != cudaSuccess ||
+        cudaMalloc(&S.flags, sizeof(int) * 2) != cudaSuccess || cudaEventCreate(&S.ev[0]) != cudaSuccess ||
+        cudaEventCreate(&S.ev[1]) != cudaSuccess) {
+      free_batch_rock(S);
+      return MR_ENOMEM;
+    }
+    S.cap = n;
+    S.part_cap = 2 * chunks;
+  }
+  if (cudaMemcpyAsync(S.inst, hin.data(), sizeof(JInst) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaMemcpyAsync(S.off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(S.ctl, hctl.data(), sizeof(RockCtl) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return MR_ECUDA;
+  const bool f32 = prec == MR_MIXED;
+  const void* kern = m == 3 ? (f32 ? joint_kernel<3, float>() : joint_kernel<3, double>())
+                            : (f32 ? joint_kernel<1, float>() : joint_kernel<1, double>());
+  const int L = n * (m == 3 ? 3 : 1);
+  const size_t smem = (size_t)L * ((f32 ? sizeof(Ops<float>) : sizeof(Ops<double>)) + sizeof(PairCtl) + sizeof(int)) +
+                      sizeof(int64_t) * 7 * (n + 1) + sizeof(int) * n;
+  if (smem > 200 * 1024) return MR_EINVAL;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return MR_ECUDA;
+  int dev = 0, nsm = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem) != cudaSuccess || per_sm < 1)
+    return MR_ECUDA;
+  A.inst = reinterpret_cast<const JInst*>(S.inst);
+  A.n = n;
+  A.m = m;
+  A.off = S.off;
+  A.dt = dt;
+  A.tol = tol;
+  A.ctl = reinterpret_cast<RockCtl*>(S.ctl);
+  A.ptr = S.ptr;
+  A.part = S.part;
+  A.flags = S.flags;
+  void* args[] = {&A};
+  const int nb = nsm * std::min(per_sm, 2);
+  cudaEventRecord(S.ev[0], stream);
+  if (cudaLaunchCooperativeKernel(kern, nb, kBlock, args, smem, stream) != cudaSuccess) return MR_ECUDA;
+  cudaEventRecord(S.ev[1], stream);
+  if (cudaMemcpyAsync(hctl.data(), S.ctl, sizeof(RockCtl) * n, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return MR_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, S.ev[0], S.ev[1]);
+  if (kernel_ms) *kernel_ms = ms;
+  mr_status st = MR_OK;
+  for (int b = 0; b < n; b++) {
+    mr_stats& s = cs[b]->stats;
+    s.rock_steps = hctl[b].steps;
+    s.rock_reject = hctl[b].rejects;
+    s.rock_stages = hctl[b].stages;
+    s.rock_matvec = hctl[b].matvecs;
+    s.rock_smax = hctl[b].smax;
+    s.rock_alg_bytes += hctl[b].bytes;
+    if (hctl[b].status && !st) {
+      cs[b]->last_error = "ROCK4 step control failed";
+      st = (mr_status)hctl[b].status;
+    }
+  }
+  return st;
 }
 
 }  // namespace mrg

@@ -88,6 +88,7 @@ def lib():
             "mr_load": [vp, C.c_char_p],
             "mr_batch_create": [C.c_int, C.POINTER(Problem), C.c_int, C.POINTER(C.c_void_p)],
             "mr_batch_run": [vp, C.c_int, C.c_double, dp, C.c_double, C.c_double, C.c_double],
+            "mr_batch_diffuse": [vp, C.c_double, C.c_double],
             "mr_batch_get_stats": [vp, C.POINTER(BatchStats)],
         }
         for name, args in sig.items():
@@ -111,10 +112,12 @@ class BatchStats(C.Structure):
                [("ms_device", C.c_double), ("ms_react_kernel", C.c_double), ("react_launches", C.c_int64)] + \
                [(n, C.c_int64) for n in ("radau_fev", "radau_jac", "radau_steps", "radau_accept", "radau_reject",
                                          "radau_newton", "radau_dec")] + \
-               [("radau_alg_flops", C.c_double), ("joint_reaction", C.c_int32), ("reserved", C.c_int32)]
+               [("radau_alg_flops", C.c_double), ("joint_reaction", C.c_int32), ("joint_diffusion", C.c_int32),
+                ("ms_adapt_phase", C.c_double), ("ms_diffuse_phase", C.c_double),
+                ("ms_diffuse_kernel", C.c_double), ("diffuse_launches", C.c_int64)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class MRError(RuntimeError):
@@ -295,7 +298,8 @@ def fp64_fma_rate():
 
 class Batch:
     """Batched serving (mr_batch_*): independent instances stepped together,
-    the reaction half steps of all of them as one joint Radau5 launch."""
+    the reaction half steps of all of them as one joint Radau5 launch and
+    the diffusion sub-step as one joint ROCK4 launch."""
 
     def __init__(self, problems, threads=0):
         arr = (Problem * len(problems))(*problems)
@@ -321,6 +325,11 @@ class Batch:
                 if buf.value:
                     msgs.append(f"[{i}] {buf.value.decode()}")
             raise MRError(rc, "mr_batch_run", "; ".join(msgs))
+
+    def diffuse(self, dt, tol=1e-6):
+        rc = lib().mr_batch_diffuse(self.h, dt, tol)
+        if rc:
+            raise MRError(rc, "mr_batch_diffuse")
 
     def stats(self):
         s = BatchStats()

@@ -1,8 +1,9 @@
-"""Batched serving (mr_batch_*): instances stepped together give exactly the
-results of stepping each instance alone (the joint Radau5 launch integrates
-every cell with the same arithmetic), the counters add up, models that cannot
-share a launch fall back to per-instance launches, and one instance is
-checked against the oracle."""
+"""Batched serving (mr_batch_*): instances stepped together give the results
+of stepping each instance alone (the joint Radau5 launch integrates every
+cell with the same arithmetic: exactly; the joint ROCK4 launch keeps each
+instance's step control but sums its error norm in another order: to
+rounding), the counters add up, models that cannot share a launch fall back
+to per-instance launches, and one instance is checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -46,6 +47,7 @@ def test_batch_equals_separate_contexts(mr):
     b.run(3, 1e-3, eta)
     st = b.stats()
     assert st["joint_reaction"] == 1 and st["steps"] == 3 and st["react_launches"] == 6
+    assert st["joint_diffusion"] == 1 and st["diffuse_launches"] == 3 and st["ms_diffuse_kernel"] > 0
     assert st["radau_fev"] > 0 and st["radau_newton"] > 0 and st["ms_device"] > 0
     updates = 0
     for _ in range(3):
@@ -56,8 +58,41 @@ def test_batch_equals_separate_contexts(mr):
     for k, c in enumerate(singles):
         kb, vb = b[k].leaves()
         ks, vs = c.leaves()
-        assert np.array_equal(kb, ks) and np.array_equal(vb, vs)
+        assert np.array_equal(kb, ks)
+        # error norms summed in another order: the same steps, states equal
+        # to a few units of rounding of the stage recurrence
+        assert b[k].stats()["rock_steps"] == c.stats()["rock_steps"]
+        for i in range(3):
+            assert np.max(np.abs(vb[i] - vs[i])) <= 1e-12 * np.max(np.abs(vs[i]))
     b.close()
+
+
+def test_joint_diffusion_alone(mr):
+    """The joint ROCK4 launch on its own (no reaction): each instance's
+    diffusion sub-step against the same instance's one-context ROCK4 driver,
+    in the FP64 and in the mixed form."""
+    for precision, tol in ((0, 1e-12), (mr.MR_MIXED, 1e-12)):
+        insts = instances(5)
+        probs = [mr.problem(2, i["J"], params=(1e-2, 1e-5, i["f"], 2e-3), precision=precision) for i, _ in insts]
+        b = mr.Batch(probs, threads=4)
+        singles = []
+        for k, (inst, u0) in enumerate(insts):
+            b[k].build(u0, inst["eta"])
+            c = mr.Context(probs[k])
+            c.build(u0, inst["eta"])
+            singles.append(c)
+        b.diffuse(2e-3)
+        st = b.stats()
+        assert st["joint_diffusion"] == 1 and st["diffuse_launches"] == 1
+        for k, c in enumerate(singles):
+            c.diffuse(2e-3)
+            assert b[k].stats()["rock_steps"] == c.stats()["rock_steps"]
+            kb, vb = b[k].leaves()
+            ks, vs = c.leaves()
+            assert np.array_equal(kb, ks)
+            for i in range(3):
+                assert np.max(np.abs(vb[i] - vs[i])) <= tol * np.max(np.abs(vs[i]))
+        b.close()
 
 
 def test_batch_instance_matches_oracle(mr):
@@ -88,7 +123,7 @@ def test_mixed_models_fall_back_per_instance(mr):
     cn = mr.Context(pn)
     cn.build(un, 1e-3)
     b.run(2, 1e-3, [inst["eta"], 1e-3])
-    assert b.stats()["joint_reaction"] == 0
+    assert b.stats()["joint_reaction"] == 0 and b.stats()["joint_diffusion"] == 0
     for _ in range(2):
         cn.strang(1e-3, 1e-3)
     kb, vb = b[1].leaves()
