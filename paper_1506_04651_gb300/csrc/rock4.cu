@@ -241,33 +241,41 @@ struct Ops {
   int kind;
 };
 
+// d: the unscaled stencil sum (sum of the neighbours minus 2D times the
+// leaf) at a regular leaf, with ih2 = 1 / h^2 of its level and beta = cl ih2;
+// L y itself at a merged row (ih2 = 1, beta = cl).  ih2 is a power of two, so
+// beta d equals cl (d ih2) exactly and the sweeps that do not keep L y save
+// the scaling multiply.
 template <typename VT>
-__device__ inline void combine(const Ops<VT>& o, int64_t r, VT Lx, double tol, double& err) {
+__device__ inline void combine(const Ops<VT>& o, int64_t r, VT d, VT ih2, VT beta, double tol, double& err) {
   switch (o.kind) {
     case K_STAGE:
-      o.out[r] = o.ca * o.a[r] + o.cb * o.b[r] + o.cl * Lx;
+      o.out[r] = o.ca * o.a[r] + o.cb * o.b[r] + beta * d;
       break;
-    case K_STAGE1:  // first step only: P_1 = y + kap_1 h L y, keeping L y
+    case K_STAGE1: {  // first step only: P_1 = y + kap_1 h L y, keeping L y
+      const VT Lx = d * ih2;
       o.lx[r] = Lx;
       o.out[r] = o.ca * o.a[r] + o.cl * Lx;
       break;
+    }
     case K_H3:
     case K_H2:
-      o.out[r] = o.ca * o.a[r] + o.cl * Lx;
+      o.out[r] = o.ca * o.a[r] + beta * d;
       break;
     case K_H1: {
-      const VT v = o.ca * o.a[r] + o.cl * Lx;  // h1 = w1 yP + z h2
+      const VT v = o.ca * o.a[r] + beta * d;  // h1 = w1 yP + z h2
       o.out[r] = v;
       o.acc[r] = o.e0 * o.a[r] + o.e1 * v + o.e2 * o.x[r];
       break;
     }
     case K_H0: {
-      const VT v = o.a[r] + o.cl * Lx;  // y_{n+1} = yP + z h1
+      const VT v = o.a[r] + beta * d;  // y_{n+1} = yP + z h1
       o.out[r] = v;
       o.acc[r] += v;
       break;
     }
     default: {  // embedded estimate e = acc + d z y_{n+1}; L y_{n+1} is kept
+      const VT Lx = d * ih2;
       o.lx[r] = Lx;
       const double ee = (double)(o.acc[r] + o.cl * Lx);
       const double sc = tol + tol * fmax(fabs((double)o.yn[r]), fabs((double)o.x[r]));
@@ -291,6 +299,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
   __shared__ double s_err2[kMaxM];
   __shared__ Ops<VT> s_ops[M];
   __shared__ int s_act[M];
+  __shared__ VT s_beta[M][kMaxL + 1];  // cl / h^2 of every level
   const int64_t N = P.N, capL = P.capL;
   if (threadIdx.x == 0) {
     C = *P.ctl;
@@ -302,7 +311,12 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
       s_ly[i] = 0;
     }
   }
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  // thread index dealt warp by warp round the blocks (warp w of block b is
+  // warp b + nb w of the grid), so that when the leaves fill the grid only
+  // partly, or a little more than once, every SM gets the same share of them
+  // (the sweeps are bound by the narrow FP64 pipe of each SM)
+  const int64_t tid = (threadIdx.x & 31) + 32 * (blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5)),
+                nth = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   const double leafb = N * (8.0 * D + 1.0);
   // vector q of species i: FP64: the state U (pool 0), W0..W2 (pool 1..3),
@@ -377,6 +391,16 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     __syncthreads();
     if (threadIdx.x < M) s_act[threadIdx.x] = ops_for(phase, threadIdx.x, s_ops[threadIdx.x]);
     __syncthreads();
+    for (int q = threadIdx.x; q < M * (kMaxL + 1); q += blockDim.x) {
+      const int i = q / (kMaxL + 1), j = q % (kMaxL + 1);
+      if (s_act[i]) {
+        if constexpr (kF64)
+          s_beta[i][j] = s_ops[i].cl * c_ih2[j];
+        else
+          s_beta[i][j] = s_ops[i].cl * c_ih2f[j];
+      }
+    }
+    __syncthreads();
   };
   // one operator sweep: regular leaves one thread each from the compact
   // table (neighbour indices loaded once for all species), merged rows G
@@ -393,11 +417,12 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
       const int4 e0 = reg[2 * q], e1 = reg[2 * q + 1];
       const int v[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
       const int64_t r = v[0];
+      const int lev = v[1 + 2 * D];
       VT ih2;
       if constexpr (kF64)
-        ih2 = c_ih2[v[1 + 2 * D]];
+        ih2 = c_ih2[lev];
       else
-        ih2 = c_ih2f[v[1 + 2 * D]];
+        ih2 = c_ih2f[lev];
 #pragma unroll
       for (int i = 0; i < M; i++) {
         if (!act[i]) continue;
@@ -405,7 +430,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
         VT sx = x[v[1]];
 #pragma unroll
         for (int f = 1; f < 2 * D; f++) sx += x[v[1 + f]];
-        combine<VT>(o[i], r, (sx - (VT)(2 * D) * x[r]) * ih2, P.tol, err[i]);
+        combine<VT>(o[i], r, sx - (VT)(2 * D) * x[r], ih2, s_beta[i][lev], P.tol, err[i]);
       }
     }
     // 2D: merged rows are taken from the last threads, which have no regular
@@ -451,7 +476,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
 #pragma unroll
           for (int u = 1; u < G; u++)
             if (i0 + u < M && sub == u) vi = v[i0 + u];
-          if (i < M && act[i]) combine<VT>(o[i], r, vi, P.tol, err_row[i0 / G]);
+          if (i < M && act[i]) combine<VT>(o[i], r, vi, (VT)1, o[i].cl, P.tol, err_row[i0 / G]);
         }
       }
     }
@@ -655,6 +680,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
   int64_t* s_coff = s_off + 4 * (n + 1);                    // [3][n + 1] the same over the active instances
   int* s_cmap = reinterpret_cast<int*>(s_coff + 3 * (n + 1));  // the active instances
   int* s_act = s_cmap + n;                                     // [L]
+  VT* s_beta = reinterpret_cast<VT*>((reinterpret_cast<uintptr_t>(s_act + L) + 7) & ~uintptr_t(7));
+  // s_beta: [L][kMaxL + 1], cl / h^2 of every level
   __shared__ double sh[kBlock];
   __shared__ int s_nact;
   for (int q = threadIdx.x; q < 4 * (n + 1); q += blockDim.x) s_off[q] = A.off[q];
@@ -666,7 +693,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
   const int64_t* creg = s_coff;
   const int64_t* cirr = s_coff + (n + 1);
   const int64_t* cleaf = s_coff + 2 * (n + 1);
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (threadIdx.x & 31) + 32 * (blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5)),
+                nth = (int64_t)gridDim.x * blockDim.x;  // dealt as in the one-instance driver
   const int lane = threadIdx.x & 31, sub = lane & (G - 1);
   // a thread's indices increase: its cursor is found once by bisection,
   // then walks forward
@@ -776,6 +804,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
     __syncthreads();
     for (int l = threadIdx.x; l < L; l += blockDim.x) s_act[l] = ops_for(phase, l, s_ops[l]);
     __syncthreads();
+    for (int q = threadIdx.x; q < L * (kMaxL + 1); q += blockDim.x) {
+      const int l = q / (kMaxL + 1), j = q % (kMaxL + 1);
+      if (s_act[l]) {
+        if constexpr (kF64)
+          s_beta[q] = s_ops[l].cl * c_ih2[j];
+        else
+          s_beta[q] = s_ops[l].cl * c_ih2f[j];
+      }
+    }
     if (threadIdx.x < 32) {
       int cnt = 0;
       int64_t c0 = 0, c1 = 0, c2 = 0;
@@ -817,15 +854,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
     __syncthreads();
   };
   // the embedded estimate of one leaf: its squared scaled error goes to E2
-  auto finish = [&](const Ops<VT>& o, const JInst& I, int sp, int64_t r, VT Lx) {
+  auto finish = [&](const Ops<VT>& o, const JInst& I, int sp, int64_t r, VT d, VT ih2, VT beta) {
     if (o.kind == K_FSAL) {
+      const VT Lx = d * ih2;
       o.lx[r] = Lx;
       const double ee = (double)(o.acc[r] + o.cl * Lx);
       const double sc = A.tol + A.tol * fmax(fabs((double)o.yn[r]), fabs((double)o.x[r]));
       I.E2[(int64_t)sp * I.capL + r] = (ee / sc) * (ee / sc);
     } else {
       double unused = 0.0;
-      combine<VT>(o, r, Lx, A.tol, unused);
+      combine<VT>(o, r, d, ih2, beta, A.tol, unused);
     }
   };
   // one operator sweep over the active instances: regular leaves one thread
@@ -842,11 +880,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
       const int4 e0 = I.reg[2 * ql], e1 = I.reg[2 * ql + 1];
       const int v[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
       const int64_t r = v[0];
+      const int lev = v[1 + 2 * D];
       VT ih2;
       if constexpr (kF64)
-        ih2 = c_ih2[v[1 + 2 * D]];
+        ih2 = c_ih2[lev];
       else
-        ih2 = c_ih2f[v[1 + 2 * D]];
+        ih2 = c_ih2f[lev];
 #pragma unroll
       for (int sp = 0; sp < M; sp++) {
         const int l = i * M + sp;
@@ -856,7 +895,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
         VT sx = x[v[1]];
 #pragma unroll
         for (int f = 1; f < 2 * D; f++) sx += x[v[1 + f]];
-        finish(o, I, sp, r, (sx - (VT)(2 * D) * x[r]) * ih2);
+        finish(o, I, sp, r, sx - (VT)(2 * D) * x[r], ih2, s_beta[l * (kMaxL + 1) + lev]);
       }
     }
     const int64_t grp = (nth - 1 - tid) / G, ngrp = nth / G;
@@ -899,7 +938,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
         const JInst& I = A.inst[i];
 #pragma unroll
         for (int sp = 0; sp < M; sp++)
-          if (s_act[i * M + sp]) finish(s_ops[i * M + sp], I, sp, r, vs[sp]);
+          if (s_act[i * M + sp]) finish(s_ops[i * M + sp], I, sp, r, vs[sp], (VT)1, s_ops[i * M + sp].cl);
       }
     }
   };
@@ -1540,7 +1579,8 @@ mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStr
                             : (f32 ? joint_kernel<1, float>() : joint_kernel<1, double>());
   const int L = n * (m == 3 ? 3 : 1);
   const size_t smem = (size_t)L * ((f32 ? sizeof(Ops<float>) : sizeof(Ops<double>)) + sizeof(PairCtl) + sizeof(int)) +
-                      sizeof(int64_t) * 7 * (n + 1) + sizeof(int) * n;
+                      sizeof(int64_t) * 7 * (n + 1) + sizeof(int) * (n + 1) +
+                      (size_t)L * (kMaxL + 1) * (f32 ? sizeof(float) : sizeof(double)) + 8;
   if (smem > 200 * 1024) return MR_EINVAL;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return MR_ECUDA;
