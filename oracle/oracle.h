@@ -14,7 +14,9 @@
  * Files:
  *   radau5.c  models f, J (Sec. 1 items I-II; BZ printed in Sec. 1; a
  *             synthetic stiff mass-action network standing in for the
- *             paper's large-mechanism case, Sec. 1 item III) and the
+ *             paper's large-mechanism case, Sec. 1 item III; a synthetic
+ *             21-species membrane model with a numerical Jacobian standing
+ *             in for the paper's STROKE model, Sec. 1 item III) and the
  *             Radau5 reaction integrator (Sec. 2.1, App. A; algorithm of
  *             Hairer-Wanner, Solving ODEs II, Sec. IV.8, cited as MR1439506)
  *   rock4.c   ROCK4-type stabilized polynomials and the linear diffusion
@@ -35,11 +37,14 @@
 #define MR_ORACLE_H
 #include <stdint.h>
 
-#define ORC_MAXM 16
+#define ORC_MAXM 32
 #define ORC_MAXL 16
 #define ORC_MAXR 32
 
-enum { ORC_MODEL_BZ = 1, ORC_MODEL_NAGUMO = 2, ORC_MODEL_LINEAR = 3, ORC_MODEL_NETWORK = 4 };
+enum { ORC_MODEL_BZ = 1, ORC_MODEL_NAGUMO = 2, ORC_MODEL_LINEAR = 3, ORC_MODEL_NETWORK = 4, ORC_MODEL_IONIC = 5 };
+
+/* IONIC: the synthetic 21-species membrane model (radau5.c) */
+#define ORC_IONIC_M 21
 
 enum {
   ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESTATE = -4,

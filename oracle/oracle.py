@@ -21,8 +21,9 @@ _lock = threading.Lock()
 _lib = None
 
 OK = 0
-MODEL_BZ, MODEL_NAGUMO, MODEL_LINEAR, MODEL_NETWORK = 1, 2, 3, 4
-MAXM = 16
+MODEL_BZ, MODEL_NAGUMO, MODEL_LINEAR, MODEL_NETWORK, MODEL_IONIC = 1, 2, 3, 4, 5
+MAXM = 32
+IONIC_M = 21
 MAXR = 32
 
 
@@ -160,6 +161,8 @@ def make_model(kind: str, m: int | None = None, params=None, K=None) -> Model:
                 md.sp[r][t] = int(sp[r, t])
             md.kf[r] = float(kf[r])
             md.kb[r] = float(kb[r])
+    elif kind == "ionic":
+        md.kind, md.m = MODEL_IONIC, IONIC_M
     else:
         raise ValueError(kind)
     return md

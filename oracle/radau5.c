@@ -23,6 +23,8 @@
 
 /* ---------------- models ---------------- */
 
+static void ionic_f(const double *y, double *f);
+
 /* BZ (Oregonator), Sec. 1 item II with a=u1, b=u2, c=u3:
  *   f_a = (-q a - a b + f c)/mu,  f_b = (b - b^2 + a (q - b))/eps,  f_c = b - c.
  * NAGUMO, Sec. 1 item I: f = k u^2 (1 - u).
@@ -41,6 +43,8 @@ void orc_model_f(const orc_model *md, const double *y, double *f) {
   } else if (md->kind == ORC_MODEL_NAGUMO) {
     double k = md->p[0], u = y[0];
     f[0] = k * u * u * (1.0 - u);
+  } else if (md->kind == ORC_MODEL_IONIC) {
+    ionic_f(y, f);
   } else if (md->kind == ORC_MODEL_NETWORK) {
     for (int i = 0; i < md->m; i++) f[i] = 0.0;
     for (int r = 0; r < md->nr; r++) {
@@ -61,10 +65,112 @@ void orc_model_f(const orc_model *md, const double *y, double *f) {
   }
 }
 
-/* Analytic Jacobian, row-major J[i*m + j] = d f_i / d y_j. */
+/* IONIC: a synthetic 21-species membrane model standing in for the paper's
+ * STROKE case (Sec. 1 item III: 21 equations, voltage-gated channels with
+ * sigmoid gates close to a Heaviside function, log evaluations, Jacobian
+ * eigenvalues down to about -1e8 near rest, numerical Jacobian).  The real
+ * model is not available; this one is designed to have those properties.
+ * All quantities are dimensionless (potentials in units of RT/F).
+ *   y[0..3]   e_k  extracellular concentration of ion k (diffuses)
+ *   y[4]      g    extracellular transmitter (diffuses)
+ *   y[5..8]   c_k  intracellular concentration of ion k
+ *   y[9]      V    membrane potential
+ *   y[10..13] a_k  activation gate of channel k
+ *   y[14..17] b_k  inactivation gate of channel k
+ *   y[18]     E    energy store
+ *   y[19]     B    buffer occupancy (ion 3)
+ *   y[20]     S    energy supply (a fixed field: f = 0)
+ * Nernst potential E_k = log(e_k / c_k) / z_k (concentrations floored at
+ * 1e-12), channel current J_k = (GL_k + G_k a_k^p_k b_k) (V - E_k), outward
+ * positive; transmitter current Jg = Gg g / (g + Kg) e_0 / (e_0 + 1) (V - Vg),
+ * carried by ion 0; pump P = Pmax E c_0 / (c_0 + K0) e_1 / (e_1 + K1), moving three of
+ * ion 0 out and two of ion 1 in per cycle (net one charge out).
+ *   V'   = -(sum_k J_k + Jg + P) / Cm
+ *   c_k' = -J_k / z_k,  e_k' = beta J_k / z_k, plus
+ *          c_0' -= Jg + 3 P, e_0' += beta (Jg + 3 P),
+ *          c_1' += 2 P,      e_1' -= 2 beta P,
+ *          c_3' -= Bt wB,  wB = kon c_3 (1 - B) - koff B
+ *   a_k' = (sig((V - Va_k) / sa_k) - a_k) / ta_k
+ *   b_k' = (sig((Vb_k - V) / sb_k) - b_k) / tb_k,  sig(x) = 1 / (1 + exp(-x))
+ *   g'   = kr sig((V - Vr) / sr) - ku g
+ *   E'   = ke (S - E) - cp P
+ *   B'   = wB,  S' = 0
+ * Invariants (exact for the reaction alone): c_k + e_k / beta for k = 0..2,
+ * c_3 + e_3 / beta + Bt B, and Cm V - sum_k z_k c_k - 2 Bt B. */
+static const double IO_Z[4] = {1.0, 1.0, -1.0, 2.0};
+static const double IO_GL[4] = {0.01, 0.3, 0.0, 0.0};
+static const double IO_G[4] = {2.0, 0.2, 0.2, 0.05};
+static const int IO_PA[4] = {3, 1, 1, 2};
+static const double IO_VA[4] = {-1.6, -2.2, -1.0, -1.2}, IO_SA[4] = {0.15, 0.2, 0.3, 0.12};
+static const double IO_VB[4] = {-2.4, -1.0, 0.0, -1.6}, IO_SB[4] = {0.12, 0.25, 0.3, 0.2};
+static const double IO_TA[4] = {1e-4, 2e-3, 5e-3, 1e-3}, IO_TB[4] = {2e-3, 5e-2, 5e-2, 2e-2};
+static const double IO_BETA = 4.0, IO_CM = 3e-9;
+static const double IO_PMAX = 0.1, IO_K0 = 1.0, IO_K1 = 0.2;
+static const double IO_GG = 2.0, IO_KG = 1.0, IO_VG = 0.0;
+static const double IO_KR = 20.0, IO_VR = -2.0, IO_SR = 0.15, IO_KU = 10.0;
+static const double IO_KE = 2.0, IO_CP = 0.5;
+static const double IO_KON = 1e3, IO_KOFF = 0.1, IO_BT = 0.05;
+static const double IO_FLOOR = 1e-12;
+
+static double io_sig(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+static void ionic_f(const double *y, double *f) {
+  const double *e = y, *c = y + 5, *a = y + 10, *b = y + 14;
+  const double g = y[4], V = y[9], E = y[18], B = y[19], S = y[20];
+  double Jk[4], Jsum = 0.0;
+  for (int k = 0; k < 4; k++) {
+    double Ek = log(fmax(e[k], IO_FLOOR) / fmax(c[k], IO_FLOOR)) / IO_Z[k];
+    double act = 1.0;
+    for (int p = 0; p < IO_PA[k]; p++) act *= a[k];
+    Jk[k] = (IO_GL[k] + IO_G[k] * act * b[k]) * (V - Ek);
+    Jsum += Jk[k];
+  }
+  double Jg = IO_GG * g / (g + IO_KG) * e[0] / (e[0] + 1.0) * (V - IO_VG);
+  double P = IO_PMAX * E * c[0] / (c[0] + IO_K0) * e[1] / (e[1] + IO_K1);
+  double wB = IO_KON * c[3] * (1.0 - B) - IO_KOFF * B;
+  for (int k = 0; k < 4; k++) {
+    f[5 + k] = -Jk[k] / IO_Z[k];
+    f[k] = IO_BETA * Jk[k] / IO_Z[k];
+  }
+  f[5] -= Jg + 3.0 * P;
+  f[0] += IO_BETA * (Jg + 3.0 * P);
+  f[6] += 2.0 * P;
+  f[1] -= 2.0 * IO_BETA * P;
+  f[8] -= IO_BT * wB;
+  f[9] = -(Jsum + Jg + P) / IO_CM;
+  for (int k = 0; k < 4; k++) {
+    f[10 + k] = (io_sig((V - IO_VA[k]) / IO_SA[k]) - a[k]) / IO_TA[k];
+    f[14 + k] = (io_sig((IO_VB[k] - V) / IO_SB[k]) - b[k]) / IO_TB[k];
+  }
+  f[4] = IO_KR * io_sig((V - IO_VR) / IO_SR) - IO_KU * g;
+  f[18] = IO_KE * (S - E) - IO_CP * P;
+  f[19] = wB;
+  f[20] = 0.0;
+}
+
+/* Numerical Jacobian by forward differences, one column per species, with
+ * the increment of Hairer and Wanner's RADAU5 code:
+ * delta_j = sqrt(1e-16 max(1e-5, |y_j|)), column j = (f(y + delta_j e_j) - f(y)) / delta_j. */
+static void jac_forward_difference(const orc_model *md, const double *y, double *J) {
+  int m = md->m;
+  double yy[ORC_MAXM], f0[ORC_MAXM], f1[ORC_MAXM];
+  orc_model_f(md, y, f0);
+  for (int j = 0; j < m; j++) yy[j] = y[j];
+  for (int j = 0; j < m; j++) {
+    double delta = sqrt(1e-16 * fmax(1e-5, fabs(y[j])));
+    yy[j] = y[j] + delta;
+    orc_model_f(md, yy, f1);
+    yy[j] = y[j];
+    for (int i = 0; i < m; i++) J[i * m + j] = (f1[i] - f0[i]) / delta;
+  }
+}
+
+/* Analytic Jacobian, row-major J[i*m + j] = d f_i / d y_j (IONIC: numerical). */
 void orc_model_jac(const orc_model *md, const double *y, double *J) {
   int m = md->m;
-  if (md->kind == ORC_MODEL_BZ) {
+  if (md->kind == ORC_MODEL_IONIC) {
+    jac_forward_difference(md, y, J);
+  } else if (md->kind == ORC_MODEL_BZ) {
     double eps = md->p[0], mu = md->p[1], ff = md->p[2], q = md->p[3];
     double a = y[0], b = y[1];
     J[0] = (-q - b) / mu; J[1] = -a / mu;                J[2] = ff / mu;

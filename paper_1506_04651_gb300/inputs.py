@@ -181,3 +181,42 @@ def network_bumps(d: int, J: int, seed: int = 5, m: int = 16, nbumps: int = 4):
                 prod = np.multiply.outer(prod, g[a])
             acc += prod
     return u.reshape(m, -1)
+
+
+# ---- the synthetic 21-species membrane model (stand-in for the paper's STROKE case)
+# Species order: e_0..e_3, g, c_0..c_3, V, a_0..a_3, b_0..b_3, E, B, S (the
+# first five diffuse).  IONIC_REST is the model's resting state with energy
+# supply S = 1 and IONIC_DEP its depolarised state (transmitter released,
+# ion 1 released to the extracellular space), both found once by integrating
+# a single cell to rest; they are initial data, not expected values.
+IONIC_M = 21
+IONIC_D = (2e-3, 2e-3, 2e-3, 1e-3, 1e-2) + (0.0,) * 16
+IONIC_REST = (14.22728634, 0.1269996353, 12.00428593, 0.15, 8.033406869e-08, 1.443178415, 14.05575009,
+              0.7989285171, 1e-05, -4.554532729, 2.790947026e-09, 7.712475299e-06, 7.149632481e-06,
+              7.23671077e-13, 0.9999999841, 0.9999993314, 0.9999997449, 0.999999616, 0.9942973554,
+              0.09090909091, 1.0)
+IONIC_DEP = (9.398867673, 3.085280159, 10.11221508, 0.1390336202, 1.99991224, 2.650283082, 13.31617996,
+             1.27194623, 2.77243063e-05, -0.4879979785, 0.9993971778, 0.9998082956, 0.8462659894,
+             0.9973559367, 1.204223034e-07, 0.1155875563, 0.8371923037, 0.003858656587, 0.9840238873,
+             0.1453865038, 1.0)
+
+
+def ionic_core(d: int, J: int, seed: int = 7, r0: float = 0.2, w: float = 0.02, amp: float = 0.02,
+               s_core: float = 0.2):
+    """Depolarised core in resting tissue: u = rest + (dep - rest) chi with
+    chi = (1 - tanh((r - r0(angle)) / w)) / 2 about the domain centre, the
+    radius perturbed by smooth seeded Fourier noise; the energy supply S is
+    1 - (1 - s_core) chi (an ischaemic core).  Shape (21, 2^(dJ))."""
+    xs = cell_centres(d, J)
+    dx = [x - 0.5 for x in xs]
+    r = np.sqrt(sum(v * v for v in dx))
+    th = np.arctan2(dx[1], dx[0]) / (2.0 * np.pi)
+    rr = r0 + _fourier(seed, th, amp=amp)
+    if d == 3:
+        ph = np.arccos(np.clip(dx[2] / np.maximum(r, 1e-300), -1.0, 1.0)) / np.pi
+        rr = rr + _fourier(seed + 1, ph, amp=amp)
+    chi = _profile(r - rr, w)
+    rest, dep = np.asarray(IONIC_REST), np.asarray(IONIC_DEP)
+    u = rest[:, None] + (dep - rest)[:, None] * chi[None, :]
+    u[20] = 1.0 - (1.0 - s_core) * chi
+    return u
