@@ -61,6 +61,12 @@ WORKLOADS = {
                                   "A+B<->C+D (seeded species, rates log-U[1e-2,1e6], D log-U[1e-4,1e-2]), "
                                   "J=8 (256^3 finest), eta=1e-3, Gaussian-bump initial state, dt=1e-3, "
                                   "Radau5 on 48x48 Newton systems, FP64"),
+    "ionic2d_J9_eta1e-3": dict(d=2, J=9, eta=1e-3, dt=1e-3, gen="ionic", seed=7, model="ionic", oracle_J=6,
+                               desc="2D synthetic 21-species membrane model (stand-in for the paper's STROKE "
+                                    "case: steep sigmoid gates, log Nernst potentials, eigenvalues to -1e8, "
+                                    "numerical Jacobian), J=9 (512^2 finest), eta=1e-3, depolarised ischaemic "
+                                    "core r=0.2 (w=0.02, smooth seeded radius noise) in resting tissue, "
+                                    "dt=1e-3, Radau5 on 63x63 Newton systems, FP64"),
 }
 BATCH = {"batch64_bz2d": dict(n=64, dt=1e-3,
                               desc="64 independent 2D BZ instances, seeded J ~ U{7..10}, f ~ U[0.9, 2.0], "
@@ -77,6 +83,8 @@ def initial_state(w, J=None):
     J = J or w["J"]
     if w["gen"] == "network":
         return I.network_bumps(w["d"], J, w["seed"])
+    if w["gen"] == "ionic":
+        return I.ionic_core(w["d"], J, w["seed"])
     if w["gen"] == "cross":
         return I.bz_cross_2d(J, w["seed"], w=w.get("w", 0.02), amp=w.get("amp", 0.01))
     if w["gen"] == "front":
@@ -92,6 +100,9 @@ def make_context(mr, w, stream, precision=0):
         c = mr.Context(mr.problem(w["d"], w["J"], model="network", D=D, precision=precision), stream=stream)
         c.set_network(sp, kf, kb)
         return c
+    if w.get("model") == "ionic":
+        return mr.Context(mr.problem(w["d"], w["J"], model="ionic", D=I.IONIC_D, precision=precision),
+                          stream=stream)
     return mr.Context(mr.problem(w["d"], w["J"], precision=precision), stream=stream)
 
 
@@ -102,13 +113,27 @@ def oracle_model(w):
     if w.get("model") == "network":
         sp, kf, kb, D = I.network_instance(w["seed"])
         return O.make_model("network", m=16, params=(sp, kf, kb)), D, 16
+    if w.get("model") == "ionic":
+        return O.make_model("ionic"), I.IONIC_D, I.IONIC_M
     return O.make_model("bz"), I.BZ_D, 3
 
 
 def moiety_basis(w):
     """Rows: a basis of the conserved moieties of the network (left null space
-    of the stoichiometric matrix) and the total amount; None for BZ."""
+    of the stoichiometric matrix) and the total amount; for the membrane
+    model its five linear invariants (ion totals c_k + e_k / beta, with the
+    buffer for ion 3, and the charge Cm V - sum z_k c_k - 2 Bt B) followed by
+    the sum of the ion totals; None for BZ."""
     from paper_1506_04651_gb300 import inputs as I
+    if w.get("model") == "ionic":
+        beta, cm, bt, z = 4.0, 3e-9, 0.05, (1.0, 1.0, -1.0, 2.0)
+        W = np.zeros((6, 21))
+        for k in range(4):
+            W[k, 5 + k], W[k, k] = 1.0, 1.0 / beta
+        W[3, 19] = bt
+        W[4, 9], W[4, 5:9], W[4, 19] = cm, [-v for v in z], -2.0 * bt
+        W[5] = W[0] + W[1] + W[2] + W[3]
+        return W
     if w.get("model") != "network":
         return None
     sp = I.network_instance(w["seed"])[0]
@@ -346,7 +371,8 @@ def run_gpu(args, w):
     if rad_ms >= rock_ms:
         ach = rad_fl / (rad_ms * 1e-3) / 1e12
         kname = ("k_radau_team (Radau5, one 16-lane team per cell, FP64)" if w.get("model") == "network"
-                 else "k_radau (Radau5, FP64)")
+                 else "k_radau_team (Radau5, one warp per cell, numerical Jacobian, FP64)"
+                 if w.get("model") == "ionic" else "k_radau (Radau5, FP64)")
         roof = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": fp64_tf,
                 "unit": "TFLOP/s", "frac": ach / fp64_tf,
                 "traffic": profiled_traffic("radau5.cu", "k_radau_bz2d_J10.md")

@@ -55,10 +55,11 @@ typedef enum {
   MR_EIO = -50
 } mr_status;
 
-enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2, MR_MODEL_NETWORK = 3 };
+enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2, MR_MODEL_NETWORK = 3, MR_MODEL_IONIC = 4 };
 enum { MR_FP64 = 0, MR_MIXED = 1 };
 
-#define MR_MAX_SPECIES 16
+#define MR_MAX_SPECIES 32
+#define MR_IONIC_SPECIES 21
 #define MR_MAX_LEVEL 16
 #define MR_MAX_REACTIONS 32
 
@@ -67,7 +68,7 @@ enum { MR_FP64 = 0, MR_MIXED = 1 };
  *   dim       d in {2, 3}
  *   J         finest level (Sec. 2.2); d*J <= 30
  *   jmin      no leaf is coarser than jmin (1 <= jmin <= J)
- *   m         number of species (BZ: 3, NAGUMO: 1, NETWORK: 2..16)
+ *   m         number of species (BZ: 3, NAGUMO: 1, NETWORK: 2..16, IONIC: 21)
  *   model     MR_MODEL_BZ: params = (eps, mu, f, q) of
  *               f_a = (-q a - a b + f c)/mu, f_b = (b - b^2 + a (q - b))/eps, f_c = b - c
  *               (Sec. 1 item II; the paper prints q = 0.02)
@@ -76,7 +77,20 @@ enum { MR_FP64 = 0, MR_MIXED = 1 };
  *               synthetic stand-in for the paper's large-mechanism case, Sec.
  *               1 item III); no params, the reactions are given by
  *               mr_set_network before the first reaction sub-step
- *   D         m diffusion coefficients
+ *             MR_MODEL_IONIC: a synthetic 21-species membrane model, the
+ *               stand-in for the paper's STROKE case (Sec. 1 item III: 21
+ *               equations, voltage-gated channels with steep sigmoid gates,
+ *               log Nernst potentials, Jacobian eigenvalues down to about
+ *               -1e8, Jacobian computed numerically); no params.  Species:
+ *               e_0..e_3 (extracellular ions), g (transmitter), c_0..c_3
+ *               (intracellular ions), V (membrane potential), a_0..a_3,
+ *               b_0..b_3 (gates), E (energy), B (buffer), S (energy supply,
+ *               f = 0).  The Jacobian is formed by forward differences, one
+ *               column per species, with the increment
+ *               sqrt(1e-16 max(1e-5, |y_j|)).
+ *   D         m diffusion coefficients (when m > 16 the species are
+ *             diffused in windows of 16; windows whose coefficients are
+ *             all zero cost nothing)
  *   precision MR_FP64, or MR_MIXED: Radau5 factorises and solves its Newton
  *             systems in FP32 and the ROCK4 stages run on FP32 vectors
  *             (Radau5 residuals, both error norms, step control, the state
@@ -245,9 +259,10 @@ mr_status mr_batch_get_stats(const mr_batch *b, mr_batch_stats *out);
 void mr_batch_destroy(mr_batch *b);
 
 /* Checkpoint and resume.  mr_save writes the current leaves to `path`:
- * a 64-byte header (8-byte magic "MRGB300\0"; int32 format version 1, dim,
+ * a 64-byte header (8-byte magic "MRGB300\0"; int32 format version 2, dim,
  * J, jmin, m, model, precision, 0; int64 leaf count; 16 zero bytes), the model parameters
- * and diffusion coefficients of the problem (8 + 16 doubles), the leaf keys
+ * and diffusion coefficients of the problem (8 + MR_MAX_SPECIES doubles;
+ * version-1 files, written with 16 coefficients, still load), the leaf keys
  * (n uint64, the key layout above) and the values (m x n doubles, species
  * major), all little-endian.  mr_load replaces the context's tree by the
  * file's leaves; the file must have been written for the same dim, J, jmin,

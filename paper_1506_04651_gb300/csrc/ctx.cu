@@ -93,7 +93,7 @@ mr_status alloc_all(mr_ctx* c) {
   A(c->irr_wf, c->irr_cap);
   for (int q = 0; q < 6; q++) A(c->work[q], (int64_t)m * c->cap_leaves);
   A(c->red, (int64_t)152 * 16 * kMaxM);
-  A(c->red_out, 64);
+  A(c->red_out, 128);
   A(c->complexity, c->cap_leaves);
   A(c->dc, 1);
   A(c->rho_bits, 1);
@@ -240,7 +240,9 @@ mr_status mr_create(const mr_problem* p, void* stream, mr_ctx** out) {
   } else if (p->model == MR_MODEL_NAGUMO) {
     if (p->m != 1 || p->nparams < 1) return MR_EINVAL;
   } else if (p->model == MR_MODEL_NETWORK) {
-    if (p->m < 2 || p->m > kMaxM) return MR_EINVAL;
+    if (p->m < 2 || p->m > 16) return MR_EINVAL;
+  } else if (p->model == MR_MODEL_IONIC) {
+    if (p->m != MR_IONIC_SPECIES) return MR_EINVAL;
   } else {
     return MR_EINVAL;
   }
@@ -452,7 +454,7 @@ mr_status mr_save(mr_ctx* c, const char* path) {
   SaveHeader h;
   memset(&h, 0, sizeof h);
   memcpy(h.magic, kMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.dim = c->prob.dim;
   h.J = c->prob.J;
   h.jmin = c->prob.jmin;
@@ -466,7 +468,7 @@ mr_status mr_save(mr_ctx* c, const char* path) {
     return MR_EIO;
   }
   bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(c->prob.params, sizeof(double), 8, f) == 8 &&
-            fwrite(c->prob.D, sizeof(double), 16, f) == 16 &&
+            fwrite(c->prob.D, sizeof(double), MR_MAX_SPECIES, f) == MR_MAX_SPECIES &&
             fwrite(keys.data(), sizeof(uint64_t), n, f) == (size_t)n &&
             fwrite(vals.data(), sizeof(double), (size_t)c->m * n, f) == (size_t)c->m * n;
   ok = (fclose(f) == 0) && ok;
@@ -485,18 +487,23 @@ mr_status mr_load(mr_ctx* c, const char* path) {
     return MR_EIO;
   }
   SaveHeader h;
-  double params[8], D[16];
-  bool ok = fread(&h, sizeof h, 1, f) == 1 && fread(params, sizeof(double), 8, f) == 8 &&
-            fread(D, sizeof(double), 16, f) == 16;
-  if (!ok) {
+  double params[8], D[MR_MAX_SPECIES];
+  if (fread(&h, sizeof h, 1, f) != 1) {
     fclose(f);
     c->last_error = "checkpoint header truncated";
     return MR_EIO;
   }
-  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) {
+  if (memcmp(h.magic, kMagic, 8) != 0 || (h.version != 1 && h.version != 2)) {
     fclose(f);
     c->last_error = "not a checkpoint of this library";
     return MR_EINVAL;
+  }
+  // version 1 stored 16 diffusion coefficients, version 2 MR_MAX_SPECIES
+  const size_t nd = h.version == 1 ? 16 : MR_MAX_SPECIES;
+  if (fread(params, sizeof(double), 8, f) != 8 || fread(D, sizeof(double), nd, f) != nd) {
+    fclose(f);
+    c->last_error = "checkpoint header truncated";
+    return MR_EIO;
   }
   if (h.dim != c->prob.dim || h.J != c->prob.J || h.jmin != c->prob.jmin || h.m != c->m ||
       h.model != c->prob.model || h.n < 1 || h.n > c->cap_leaves) {
@@ -506,8 +513,8 @@ mr_status mr_load(mr_ctx* c, const char* path) {
   }
   std::vector<uint64_t> keys(h.n);
   std::vector<double> vals((size_t)c->m * h.n);
-  ok = fread(keys.data(), sizeof(uint64_t), h.n, f) == (size_t)h.n &&
-       fread(vals.data(), sizeof(double), (size_t)c->m * h.n, f) == (size_t)c->m * h.n;
+  const bool ok = fread(keys.data(), sizeof(uint64_t), h.n, f) == (size_t)h.n &&
+                  fread(vals.data(), sizeof(double), (size_t)c->m * h.n, f) == (size_t)c->m * h.n;
   fclose(f);
   if (!ok) {
     c->last_error = "checkpoint data truncated";

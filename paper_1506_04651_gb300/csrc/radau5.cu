@@ -786,6 +786,7 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   C.fnewt = std::max(10.0 * 1e-16 / C.rt, std::min(0.03, sqrt(C.rt)));
   C.ifnewt = 1.0 / C.fnewt;
   if (c->prob.model == MR_MODEL_NETWORK) return react_network(c, C, dt);
+  if (c->prob.model == MR_MODEL_IONIC) return react_ionic(c, C, dt);
   MR_CUDA(c, cudaMemsetAsync(c->dc->radau, 0, sizeof(c->dc->radau), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->work_next, 0, sizeof(int), c->stream));

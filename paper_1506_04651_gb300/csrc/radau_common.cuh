@@ -1,5 +1,5 @@
 // Pieces shared by the Radau5 kernels (one thread per cell, csrc/radau5.cu;
-// one team of 16 lanes per cell for larger systems, csrc/radau5_net.cu):
+// one team of 16 or 32 lanes per cell for larger systems, csrc/radau5_net.cu):
 // the method's constants as the kernels take them, per-cell counters, and
 // two small helpers.
 #pragma once
@@ -45,8 +45,9 @@ __device__ inline double pow08(double x) {
 // kernel-side constants from radau_constants' array (tolerances unset)
 RadauC constants_from(const double* rc);
 
-// Reaction sub-step of the network model (team kernel); C carries the
-// transformed tolerances of the call.
+// Reaction sub-steps of the network and membrane models (team kernels); C
+// carries the transformed tolerances of the call.
 mr_status react_network(mr_ctx* c, const RadauC& C, double dt);
+mr_status react_ionic(mr_ctx* c, const RadauC& C, double dt);
 
 }  // namespace mrg

@@ -1407,7 +1407,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // kernels for 1, 3 and up to 16 species (unused species of the 16-wide
-  // kernel are marked done)
+  // kernel are marked done); more species run in windows of 16
   const int M = m == 1 ? 1 : (m == 3 ? 3 : 16);
   // FP64 stage vectors, or FP32 in the mixed form
   const bool f32 = c->prob.precision == MR_MIXED;
@@ -1428,57 +1428,65 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
                                          : (const void*)k_rock_persistent<3, 16, float>));
   MR_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return MR_ECUDA;
-  // enough blocks to cover the leaves, at most what is co-resident
-  const int64_t want = std::max<int64_t>(1, (N + kBlock - 1) / kBlock);
   // enough blocks to cover the leaves, at most two co-resident per SM
+  const int64_t want = std::max<int64_t>(1, (N + kBlock - 1) / kBlock);
   const int nb = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 2));
-  RockCtl hctl;
-  memset(&hctl, 0, sizeof hctl);
-  for (int i = 0; i < kMaxM; i++) {
-    hctl.h[i] = dt;
-    hctl.done[i] = i >= m || !(dt > 0.0) || c->prob.D[i] == 0.0 || N == 0;
-  }
-  RockCtl* dctl = reinterpret_cast<RockCtl*>(c->rock_ctl);
-  MR_CUDA(c, cudaMemcpyAsync(dctl, &hctl, sizeof hctl, cudaMemcpyHostToDevice, c->stream));
-  P.m = m;
-  P.D = c->d;
-  P.nb = nb;
-  P.N = N;
-  P.capL = c->cap_leaves;
-  P.dt = dt;
-  P.tol = tol;
-  P.rho = c->rho;
-  for (int i = 0; i < m; i++) P.Dc[i] = c->prob.D[i];
-  P.U = c->tb[c->cur].U;
-  for (int q = 0; q < 6; q++) P.W[q] = c->work[q];
-  P.part = c->red;
-  P.ctl = dctl;
-  IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_wf, c->irr_slot};
-  const int4* reg = c->reg_tab;
-  const int32_t* irr_leaf = c->irr_leaf;
-  int64_t nirr = c->stats.irregular_rows;
-  int64_t nreg = N - nirr;
-  void* args[] = {&P, (void*)&reg, &nreg, &R, (void*)&irr_leaf, &nirr};
-  MR_CUDA(c, cudaEventRecord(c->tev[0], c->stream));
-  MR_CUDA(c, cudaLaunchCooperativeKernel(kern, nb, kBlock, args, 0, c->stream));
-  MR_CUDA(c, cudaEventRecord(c->tev[1], c->stream));
-  c->launches++;
-  MR_CUDA(c, cudaMemcpyAsync(&hctl, dctl, sizeof hctl, cudaMemcpyDeviceToHost, c->stream));
-  MR_CUDA(c, cudaStreamSynchronize(c->stream));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]);
   mr_stats& S = c->stats;
-  S.rock_steps = hctl.steps;
-  S.rock_reject = hctl.rejects;
-  S.rock_stages = hctl.stages;
-  S.rock_matvec = hctl.matvecs;
-  S.rock_smax = hctl.smax;
-  S.rock_kernel_ms += ms;
-  S.rock_kernel_launches++;
-  S.rock_alg_bytes += hctl.bytes;
-  if (hctl.status) {
-    c->last_error = "ROCK4 step control failed";
-    return (mr_status)hctl.status;
+  S.rock_steps = S.rock_reject = S.rock_stages = S.rock_matvec = 0;
+  S.rock_smax = 0;
+  for (int w0 = 0; w0 < m; w0 += M) {
+    const int mw = std::min(M, m - w0);  // species of this window
+    bool any = false;
+    for (int i = 0; i < mw; i++) any = any || c->prob.D[w0 + i] != 0.0;
+    if (!any && w0 > 0) continue;  // nothing diffuses in this window
+    RockCtl hctl;
+    memset(&hctl, 0, sizeof hctl);
+    for (int i = 0; i < kMaxM; i++) {
+      hctl.h[i] = dt;
+      hctl.done[i] = i >= mw || !(dt > 0.0) || c->prob.D[w0 + i] == 0.0 || N == 0;
+    }
+    RockCtl* dctl = reinterpret_cast<RockCtl*>(c->rock_ctl);
+    MR_CUDA(c, cudaMemcpyAsync(dctl, &hctl, sizeof hctl, cudaMemcpyHostToDevice, c->stream));
+    P.m = mw;
+    P.D = c->d;
+    P.nb = nb;
+    P.N = N;
+    P.capL = c->cap_leaves;
+    P.dt = dt;
+    P.tol = tol;
+    P.rho = c->rho;
+    for (int i = 0; i < mw; i++) P.Dc[i] = c->prob.D[w0 + i];
+    // the window's species: rows w0.. of the state and of every work buffer
+    P.U = c->tb[c->cur].U + (int64_t)w0 * c->cap_leaves;
+    for (int q = 0; q < 6; q++) P.W[q] = c->work[q] + (int64_t)w0 * c->cap_leaves;
+    P.part = c->red;
+    P.ctl = dctl;
+    IrrRows R{c->irr_cnt, c->irr_col, c->irr_w, c->irr_wf, c->irr_slot};
+    const int4* reg = c->reg_tab;
+    const int32_t* irr_leaf = c->irr_leaf;
+    int64_t nirr = c->stats.irregular_rows;
+    int64_t nreg = N - nirr;
+    void* args[] = {&P, (void*)&reg, &nreg, &R, (void*)&irr_leaf, &nirr};
+    MR_CUDA(c, cudaEventRecord(c->tev[0], c->stream));
+    MR_CUDA(c, cudaLaunchCooperativeKernel(kern, nb, kBlock, args, 0, c->stream));
+    MR_CUDA(c, cudaEventRecord(c->tev[1], c->stream));
+    c->launches++;
+    MR_CUDA(c, cudaMemcpyAsync(&hctl, dctl, sizeof hctl, cudaMemcpyDeviceToHost, c->stream));
+    MR_CUDA(c, cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]);
+    S.rock_steps += hctl.steps;
+    S.rock_reject += hctl.rejects;
+    S.rock_stages += hctl.stages;
+    S.rock_matvec += hctl.matvecs;
+    S.rock_smax = std::max(S.rock_smax, (int32_t)hctl.smax);
+    S.rock_kernel_ms += ms;
+    S.rock_kernel_launches++;
+    S.rock_alg_bytes += hctl.bytes;
+    if (hctl.status) {
+      c->last_error = "ROCK4 step control failed";
+      return (mr_status)hctl.status;
+    }
   }
   return MR_OK;
 }

@@ -14,9 +14,10 @@ import numpy as np
 from . import build as _build
 
 MR_OK = 0
-MR_MODEL_BZ, MR_MODEL_NAGUMO, MR_MODEL_NETWORK = 1, 2, 3
+MR_MODEL_BZ, MR_MODEL_NAGUMO, MR_MODEL_NETWORK, MR_MODEL_IONIC = 1, 2, 3, 4
+IONIC_SPECIES = 21
 MR_FP64, MR_MIXED = 0, 1
-MAX_SPECIES, MAX_LEVEL = 16, 16
+MAX_SPECIES, MAX_LEVEL = 32, 16
 
 STATUS = {0: "MR_OK", -1: "MR_EINVAL", -2: "MR_ENOMEM", -3: "MR_ECUDA", -4: "MR_ESTATE",
           -10: "MR_ERADAU_HMIN", -11: "MR_ERADAU_MAXSTEPS", -12: "MR_ERADAU_SINGULAR",
@@ -148,6 +149,11 @@ def problem(dim, J, model="bz", params=None, D=None, jmin=2, precision=MR_FP64, 
         # reactions are set on the context (Context.set_network); D has m entries
         p.model, p.m = MR_MODEL_NETWORK, len(D)
         params = ()
+    elif model == "ionic":
+        # the synthetic 21-species membrane model; D has 21 entries
+        p.model, p.m = MR_MODEL_IONIC, IONIC_SPECIES
+        params = ()
+        assert D is not None and len(D) == IONIC_SPECIES
     else:
         raise ValueError(model)
     p.nparams = len(params)
