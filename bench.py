@@ -333,14 +333,19 @@ def run_gpu(args, w):
         pg.barrier()
     torch.cuda.synchronize()
     leaves, nmax = 0, len(k_start)
+    phase_sum = {"adapt_and_tables": 0.0, "react_both_halves": 0.0, "diffuse": 0.0}
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record(stream)
         step()
         ev1[k].record(stream)
-        nk = ctx.stats()["leaves"]
+        sk = ctx.stats()
+        nk = sk["leaves"]
         leaves += nk
         nmax = max(nmax, nk)
+        phase_sum["adapt_and_tables"] += sk["ms_adapt"]
+        phase_sum["react_both_halves"] += sk["ms_react"]
+        phase_sum["diffuse"] += sk["ms_diffuse"]
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -397,8 +402,11 @@ def run_gpu(args, w):
                "rock": {"ms": rock_ms, "launches": rock_n,
                         "gbs": rock_b / max(rock_ms, 1e-9) / 1e6},
                "step_ms": ms / args.steps,
-               "last_step_phase_ms": {"adapt_and_tables": st1["ms_adapt"], "react_both_halves": st1["ms_react"],
-                                      "diffuse": st1["ms_diffuse"]}}
+               # CUDA-event phases of every timed step, averaged; the rest of
+               # the step is host time between the phases (synchronisations,
+               # launches) and the call's entry and return
+               "phase_ms_per_step": {k: v / args.steps for k, v in phase_sum.items()},
+               "host_gap_ms_per_step": ms / args.steps - sum(phase_sum.values()) / args.steps}
 
     # end to end through the C-ABI with host buffers, replaying the timed
     # steps from the same starting state: every step the state goes in from

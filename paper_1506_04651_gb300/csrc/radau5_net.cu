@@ -243,34 +243,110 @@ struct IonicTeam {
   struct Params {
     int unused;
   };
-  double* sx;  // [4][32] states handed to the lanes that evaluate f
-  double* sf;  // [4][32] their results (row 3: f at the current state, for the Jacobian)
+  double* sx;  // [4][32] the state handed to the lanes that form Jacobian columns
+  double* sf;  // [4][32] row 3: f at the current state, for the Jacobian
   int t;
   unsigned mask;
   __device__ IonicTeam(const Params&, int lane, unsigned msk, double* scratch)
       : sx(scratch), sf(scratch + 4 * 32), t(lane), mask(msk) {}
-  __device__ double rhs(double u) const {
-    sx[t] = u;
-    __syncwarp(mask);
-    if (t == 0) io::rhs(sx, sf);
-    __syncwarp(mask);
-    const double r = t < MR ? sf[t] : 0.0;
-    __syncwarp(mask);
-    return r;
+
+  // f_t of the state whose component t this lane holds, spread over the
+  // team in two rounds.  Round 1, one uniform instruction stream: lanes 0..3
+  // the four channel currents J_k (a log each), lanes 4..11 the gate
+  // sigmoids, lane 12 the release sigmoid (an exp each), lane 13 the
+  // transmitter current, lane 14 the pump, lane 15 the buffer rate.  Round 2:
+  // lane t assembles f_t from the broadcast terms.
+  __device__ double rhs(double x) const {
+    using namespace io;
+    const double V = __shfl_sync(mask, x, 9);
+    int a = t, b = t, cI = t, dI = t;  // the four inputs this lane gathers
+    if (t < 4) {
+      a = t;       // e_k
+      b = 5 + t;   // c_k
+      cI = 10 + t; // a_k
+      dI = 14 + t; // b_k
+    } else if (t == 13) {
+      a = 4;       // g
+      b = 0;       // e_0
+    } else if (t == 14) {
+      a = 5;       // c_0
+      b = 1;       // e_1
+      cI = 18;     // E
+    } else if (t == 15) {
+      a = 8;       // c_3
+      b = 19;      // B
+    }
+    const double A = __shfl_sync(mask, x, a), Bv = __shfl_sync(mask, x, b);
+    const double Cv = __shfl_sync(mask, x, cI), Dv = __shfl_sync(mask, x, dI);
+    // every lane evaluates the same three pieces from its own arguments
+    const int k = t & 3;
+    const bool ion = t < 4;
+    const double lg = log(ion ? fmax(A, kFloor) / fmax(Bv, kFloor) : 1.0);
+    double arg = 0.0;  // sigmoid argument of lanes 4..12
+    if (t >= 4 && t < 8)
+      arg = (V - kVA[k]) * kISA[k];
+    else if (t >= 8 && t < 12)
+      arg = (kVB[k] - V) * kISB[k];
+    else if (t == 12)
+      arg = (V - kVr) * kISr;
+    const double sg = 1.0 / (1.0 + exp(-arg));
+    const double n1 = t == 13 ? A : Bv, d1 = t == 13 ? kKg : (t == 14 ? kK0 : 1.0);
+    const double n2 = t == 13 ? Bv : A, d2 = t == 13 ? 1.0 : (t == 14 ? kK1 : 1.0);
+    double val;
+    if (ion) {
+      double act = 1.0;
+#pragma unroll
+      for (int q = 0; q < 3; q++)
+        if (q < kPA[k]) act *= Cv;
+      val = (kGL[k] + kG[k] * act * Dv) * (V - lg * kIZ[k]);
+    } else if (t < 13) {
+      val = sg;
+    } else if (t == 13) {
+      val = kGg * A / (A + d1) * Bv / (Bv + d2) * (V - kVg);
+    } else if (t == 14) {
+      val = kPmax * Cv * A / (A + d1) * Bv / (Bv + d2);
+    } else {
+      val = kKon * A * (1.0 - Bv) - kKoff * Bv;
+    }
+    (void)n1;
+    (void)n2;
+    // round 2
+    const double J0 = __shfl_sync(mask, val, 0), J1 = __shfl_sync(mask, val, 1);
+    const double J2 = __shfl_sync(mask, val, 2), J3 = __shfl_sync(mask, val, 3);
+    const double Jg = __shfl_sync(mask, val, 13), P = __shfl_sync(mask, val, 14);
+    const double wB = __shfl_sync(mask, val, 15);
+    const double sown = __shfl_sync(mask, val, (t >= 10 && t < 18) ? t - 6 : 12);
+    const double Sx = __shfl_sync(mask, x, 20);
+    const double Jt = t < 4 ? (t == 0 ? J0 : t == 1 ? J1 : t == 2 ? J2 : J3)
+                            : (t == 5 ? J0 : t == 6 ? J1 : t == 7 ? J2 : J3);
+    double f = 0.0;
+    if (t < 4) {
+      f = kBeta * Jt * kIZ[t];
+      if (t == 0) f += kBeta * (Jg + 3.0 * P);
+      if (t == 1) f -= 2.0 * kBeta * P;
+    } else if (t == 4) {
+      f = kKr * sown - kKu * x;
+    } else if (t < 9) {
+      f = -Jt * kIZ[t - 5];
+      if (t == 5) f -= Jg + 3.0 * P;
+      if (t == 6) f += 2.0 * P;
+      if (t == 8) f -= kBt * wB;
+    } else if (t == 9) {
+      f = -((((J0 + J1) + J2) + J3) + Jg + P) * kICm;
+    } else if (t < 14) {
+      f = (sown - x) * kITA[t - 10];
+    } else if (t < 18) {
+      f = (sown - x) * kITB[t - 14];
+    } else if (t == 18) {
+      f = kKe * (Sx - x) - kCp * P;
+    } else if (t == 19) {
+      f = wB;
+    }
+    return f;
   }
   __device__ void rhs3(const double x[3], double F[3]) const {
 #pragma unroll
-    for (int s = 0; s < 3; s++) sx[s * 32 + t] = x[s];
-    __syncwarp(mask);
-    if (t < 3) {
-      const double* xs = sx + t * 32;
-      double* fs = sf + t * 32;
-      io::rhs(xs, fs);
-    }
-    __syncwarp(mask);
-#pragma unroll
-    for (int s = 0; s < 3; s++) F[s] = t < MR ? sf[s * 32 + t] : 0.0;
-    __syncwarp(mask);
+    for (int s = 0; s < 3; s++) F[s] = rhs(x[s]);
   }
   // forward differences: lane j perturbs species j by
   // delta_j = sqrt(1e-16 max(1e-5, |y_j|)) and writes column j,
