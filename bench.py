@@ -334,6 +334,7 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
     leaves, nmax = 0, len(k_start)
     phase_sum = {"adapt_and_tables": 0.0, "react_both_halves": 0.0, "diffuse": 0.0}
+    nodes_sum = 0
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record(stream)
@@ -346,6 +347,7 @@ def run_gpu(args, w):
         phase_sum["adapt_and_tables"] += sk["ms_adapt"]
         phase_sum["react_both_halves"] += sk["ms_react"]
         phase_sum["diffuse"] += sk["ms_diffuse"]
+        nodes_sum += sk["nodes"]
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -392,6 +394,20 @@ def run_gpu(args, w):
                 if args.workload == DEFAULT else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s",
                 "launches": rock_n, "ms_per_launch": rock_ms / max(rock_n, 1)}
+    # adaptation: algorithmic bytes per step = for the tree before and after
+    # (about the same size), every node's m values (8 B each), code (4 B) and
+    # level (1 B) read or written once, plus its tag byte
+    m_sp = ctx.m
+    adapt_ms = phase_sum["adapt_and_tables"] / args.steps
+    adapt_b = 2.0 * (nodes_sum / args.steps) * (8.0 * m_sp + 4.0 + 1.0 + 1.0)
+    adapt_ach = adapt_b / (adapt_ms * 1e-3) / 1e9 if adapt_ms else 0.0
+    roof_adapt = {"bound": "hbm", "kernel": "adaptation and operator tables (the whole phase)",
+                  "achieved": adapt_ach, "peak": hbm or 6800.0, "unit": "GB/s",
+                  "frac": adapt_ach / (hbm or 6800.0),
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s",
+                  "note": "algorithmic bytes (values, code, level and tag of every node of the old and new tree, "
+                          "once) over the phase's event time per step; the phase is launch- and latency-bound "
+                          "(tens of small kernels, a few host synchronisations to size the new tree)"}
     rock_ach = rock_b / (rock_ms * 1e-3) / 1e9 if rock_ms else 0.0
     roof_rock = {"bound": "hbm", "kernel": "k_rock_persistent (ROCK4 sweeps, whole diffusion sub-step)",
                  "achieved": rock_ach, "peak": hbm or 6800.0, "unit": "GB/s", "frac": rock_ach / (hbm or 6800.0),
@@ -476,7 +492,7 @@ def run_gpu(args, w):
                        "l2": "flushed between timed steps (256 MB write)",
                        "leaves_last_step": st["leaves"], "compression_ratio": st["compression_ratio"],
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "roofline": roof, "roofline_rock4": roof_rock, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "roofline_rock4": roof_rock, "roofline_adapt": roof_adapt, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "mixed": mixed,
             "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
     if conservation:

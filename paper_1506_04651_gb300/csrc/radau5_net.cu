@@ -278,7 +278,7 @@ struct IonicTeam {
     }
     const double A = __shfl_sync(mask, x, a), Bv = __shfl_sync(mask, x, b);
     const double Cv = __shfl_sync(mask, x, cI), Dv = __shfl_sync(mask, x, dI);
-    // every lane evaluates the same three pieces from its own arguments
+    // every lane evaluates the log and the sigmoid from its own arguments
     const int k = t & 3;
     const bool ion = t < 4;
     const double lg = log(ion ? fmax(A, kFloor) / fmax(Bv, kFloor) : 1.0);
@@ -290,8 +290,9 @@ struct IonicTeam {
     else if (t == 12)
       arg = (V - kVr) * kISr;
     const double sg = 1.0 / (1.0 + exp(-arg));
-    const double n1 = t == 13 ? A : Bv, d1 = t == 13 ? kKg : (t == 14 ? kK0 : 1.0);
-    const double n2 = t == 13 ? Bv : A, d2 = t == 13 ? 1.0 : (t == 14 ? kK1 : 1.0);
+    // saturation constants of the transmitter current (lane 13) and the pump (lane 14)
+    const double d1 = t == 13 ? kKg : (t == 14 ? kK0 : 1.0);
+    const double d2 = t == 13 ? 1.0 : (t == 14 ? kK1 : 1.0);
     double val;
     if (ion) {
       double act = 1.0;
@@ -308,8 +309,6 @@ struct IonicTeam {
     } else {
       val = kKon * A * (1.0 - Bv) - kKoff * Bv;
     }
-    (void)n1;
-    (void)n2;
     // round 2
     const double J0 = __shfl_sync(mask, val, 0), J1 = __shfl_sync(mask, val, 1);
     const double J2 = __shfl_sync(mask, val, 2), J3 = __shfl_sync(mask, val, 3);
