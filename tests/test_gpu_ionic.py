@@ -22,7 +22,7 @@ differ and the bound is the step tolerance itself, atol + rtol |y|; such
 cells must stay under 1%.  Adaptations are bit-identical; species with D = 0 are untouched
 by the diffusion; a diffusing species in the second window (species 16..20)
 is diffused as the oracle does; the mixed form stays within 1e-5 relative L1
-of the FP64 oracle."""
+of the FP64 oracle; the bench's full-size 2D J = 9 step agrees on every leaf."""
 import numpy as np
 import pytest
 
@@ -132,3 +132,37 @@ def test_mixed_form(mr):
             den = np.sum(vol * np.abs(v_o[i]))
             if den > 0:
                 assert np.sum(vol * np.abs(v_g[i] - v_o[i])) / den <= 1e-5
+
+
+def test_full_size_step(mr):
+    """The bench's 2D J = 9 workload: the initial grid and one Strang step
+    against the oracle on every leaf.  Grids identical; every component
+    within the step tolerance atol + rtol |y| of each half step, and 99% of
+    the leaves within the Newton bound (see above) of the two half steps;
+    the five linear invariants' domain integrals as the oracle's to 1e-10."""
+    import os
+    import torch
+    J, eta = 9, 1e-3
+    u0 = I.ionic_core(2, J, 7)
+    T = O.Tree(2, J, 21, jmin=2)
+    T.set_full(u0)
+    assert T.adapt(eta) == 0
+    c = mr.Context(mr.problem(2, J, model="ionic", D=I.IONIC_D), stream=torch.cuda.current_stream())
+    c.build(torch.from_numpy(u0).cuda(), eta)
+    k_o, v_o = T.leaves()
+    k_g, v_g = c.leaves()
+    assert np.array_equal(k_o, k_g) and np.array_equal(v_o, v_g)
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        assert T.strang(O.make_model("ionic"), I.IONIC_D, 1e-3, eta) == 0
+    finally:
+        O.set_threads(1)
+    c.strang(1e-3, eta)
+    k_o, v_o = T.leaves()
+    k_g, v_g = c.leaves()
+    assert np.array_equal(k_o, k_g)
+    diff = np.abs(v_g - v_o)
+    assert np.all(diff <= 2 * 1e-6 * (1.0 + np.abs(v_o)))
+    ok = np.all(diff <= 2 * 4 * 3.2e-8 * (1.0 + np.abs(v_o)), axis=0)
+    assert np.mean(ok) >= 0.99
+    np.testing.assert_allclose(c.mass(), T.mass(), rtol=1e-10, atol=1e-14)
