@@ -715,6 +715,9 @@ def main():
     ap.add_argument("--J", type=int, default=0,
                     help="run the workload at another finest level (profiling captures of a smaller case); "
                          "the line's config records it")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="batched workload: the first N of its seeded instances (profiling captures of a "
+                         "smaller case); the line's config records it")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -722,7 +725,11 @@ def main():
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-instance workloads"}))
             return
-        run_batch(args, BATCH[args.workload])
+        b = BATCH[args.workload]
+        if args.instances and args.instances != b["n"]:
+            b = dict(b, n=max(1, min(args.instances, b["n"])),
+                     desc=b["desc"] + f" -- run with the first {args.instances} instances")
+        run_batch(args, b)
         return
     w = WORKLOADS[args.workload]
     if args.J and args.J != w["J"]:
