@@ -141,6 +141,10 @@ def test_batch_rejects_bad_arguments(mr):
     with pytest.raises(mr.MRError) as e:
         b.run(1, -1e-3, [1e-3])
     assert e.value.code == -1
+    for bad in ((0.0, 1e-6), (float("inf"), 1e-6), (1e-3, 0.0)):
+        with pytest.raises(mr.MRError) as e:
+            b.diffuse(*bad)
+        assert e.value.code == -1
 
 
 def test_full_batch_config_one_step(mr):

@@ -62,3 +62,30 @@ def test_load_rejects_other_problem_and_bad_files(mr, tmp_path):
     assert e.value.code == -50
     keys1, vals1 = a.leaves()  # failed loads leave the context as it was
     assert np.array_equal(keys0, keys1) and np.array_equal(vals0, vals1)
+
+
+def test_version_1_files_still_load(mr, tmp_path):
+    """Format version 1 stored 16 diffusion coefficients after the 8
+    parameters (version 2 stores MR_MAX_SPECIES = 32): a version-1 file,
+    rebuilt here from a version-2 one, loads to the same leaves."""
+    import struct
+    J = 7
+    a = mr.Context(mr.problem(2, J))
+    a.build(I.bz_front_2d(J, 1), 1e-3)
+    path = str(tmp_path / "v2.mrgb")
+    a.save(path)
+    raw = open(path, "rb").read()
+    assert struct.unpack_from("<i", raw, 8)[0] == 2
+    header = bytearray(raw[:64])
+    struct.pack_into("<i", header, 8, 1)
+    params = raw[64:64 + 8 * 8]
+    d16 = raw[64 + 8 * 8:64 + 8 * 8 + 16 * 8]
+    rest = raw[64 + 8 * 8 + 32 * 8:]
+    v1 = tmp_path / "v1.mrgb"
+    v1.write_bytes(bytes(header) + params + d16 + rest)
+    b = mr.Context(mr.problem(2, J))
+    b.build(I.bz_front_2d(J, 2), 1e-3)
+    b.load(str(v1))
+    ka, va = a.leaves()
+    kb, vb = b.leaves()
+    assert np.array_equal(ka, kb) and np.array_equal(va, vb)
