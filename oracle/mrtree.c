@@ -102,8 +102,10 @@ static double wpred(int a, int o) {
   return ((o == -1) == (a == 0)) ? 0.125 : -0.125;
 }
 
+/* d in {2, 3}: the dimensions of the method's problems and of the GPU path
+ * (the one-dimensional case is not supported) */
 orc_tree *orc_tree_new(int d, int J, int jmin, int m) {
-  if (d < 1 || d > 3 || J < 1 || J > ORC_MAXL || m < 1 || m > ORC_MAXM) return NULL;
+  if (d < 2 || d > 3 || J < 1 || J > ORC_MAXL || m < 1 || m > ORC_MAXM) return NULL;
   if ((int64_t)d * J > 48 || jmin < 1 || jmin > J) return NULL;
   orc_tree *T = calloc(1, sizeof *T);
   T->d = d; T->J = J; T->jmin = jmin; T->m = m;

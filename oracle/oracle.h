@@ -30,8 +30,11 @@
  *             discretise, App. C), Strang step (Sec. 2.1), mass.
  *
  * Parity pins: see tests/test_oracle_*.py.  Every function is pinned by a
- * closed form, an invariant or brute force; none is "parity unpinned" except
- * the whole multi-step BZ trajectory, which has no published worked example.
+ * closed form, an invariant or brute force.  The whole multi-step trajectory
+ * (adaptation, Radau5, ROCK4, splitting) is pinned by the exact travelling
+ * front of the NAGUMO model; the multi-step BZ trajectory itself has no
+ * closed form and no published worked example ("parity unpinned" for that
+ * model's trajectory beyond its per-step pins).  Trees are 2D or 3D.
  */
 #ifndef MR_ORACLE_H
 #define MR_ORACLE_H
