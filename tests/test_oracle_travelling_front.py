@@ -13,7 +13,7 @@ long as the front's tails stay far from the walls.
 Here k = 20, D = 2e-3 (lambda = 70.7, c = 0.1414), a front along y at
 x0 = 0.35 on the 2D J = 9 grid (lambda h = 0.14), eta = 1e-4, dt = 2e-3,
 100 Strang steps: the integral must grow by c t within 1% (discretisation
-errors in space, time and splitting, measured: 0.03%), and u must stay in
+errors in space, time and splitting, measured: 0.013%), and u must stay in
 [0, 1] up to rounding (no overshoot of the stabilised diffusion at the
 level jumps)."""
 import numpy as np
