@@ -33,15 +33,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1506_04651_gb300.inputs import CROSS_J10  # noqa: E402  (generator parameters only)
+
 METRIC = "leaf-cell Strang updates/s on 1 GB300, mixed vs FP64 at rel-L1 ≤1e-5; % roofline"
 UNIT = "leaf-updates/s"
 
 WORKLOADS = {
-    "bz2d_J10_eta1e-3": dict(d=2, J=10, eta=1e-3, dt=1e-3, gen="cross", seed=2, w=0.01, amp=0.1,
+    "bz2d_J10_eta1e-3": dict(d=2, J=10, eta=1e-3, dt=1e-3, gen="cross", seed=2, **CROSS_J10,
                              desc="2D BZ, J=10 (1024^2 finest), eta=1e-3, graded, two crossing "
-                                  "tanh fronts (w=0.01) with smooth seeded position noise (8 modes, "
-                                  "amplitude 0.1): ~10% of finest cells are leaves; dt=1e-3, FP64"),
-    "bz2d_J10_cm": dict(d=2, J=10, eta=0.0, dt=1e-3, gen="cross", seed=2, w=0.01, amp=0.1, oracle_J=8,
+                                  f"tanh fronts (w={CROSS_J10['w']}) with smooth seeded position noise (8 modes, "
+                                  f"amplitude {CROSS_J10['amp']}): 12-17% of finest cells are leaves over steps "
+                                  "5-25 (15% initially); dt=1e-3, FP64"),
+    "bz2d_J10_cm": dict(d=2, J=10, eta=0.0, dt=1e-3, gen="cross", seed=2, **CROSS_J10, oracle_J=8,
                         desc="2D BZ on the uniform 1024^2 grid (Cartesian mesh: J=10, eta=0), the same crossing "
                              "fronts as the adaptive J=10 workload, dt=1e-3, FP64: the CM side of the paper's "
                              "MR-versus-CM comparison"),

@@ -315,7 +315,11 @@ mr_status mr_rock4_coefficients(int s, double *mu, double *nu, double *kap, doub
  * 512-byte static device array that every GPU which loads this library holds
  * until the process exits; no cudaMalloc/cudaFree or allocating library call is
  * made.  The first call on a device looks up that array's device address and
- * caches it, so make that first call before any stream capture.  All calls share
+ * caches it, so make that first call before any stream capture; the cached
+ * address belongs to the device's primary context and is not valid after
+ * cudaDeviceReset (do not call this entry point after a reset in the same
+ * process).  The work-queue head is 64-bit, so the tickets the grid draws past
+ * the last cell cannot wrap at any n up to the maximum.  All calls share
  * the array (it keeps the last call's contents; each call clears it first), so
  * calls whose work overlaps on the GPU -- other streams, other host threads --
  * race on it and must be serialised by the caller.

@@ -23,7 +23,7 @@
  *              Cartesian mesh; coefficients depend on the neighbour's level.
  *   Sec. 2.1   Strang step U_{n+1} = R_{dt/2} D_dt R_{dt/2} U_n.
  *
- * Readings where the paper is silent (each listed in the design notes):
+ * Readings where the paper is silent:
  *   - boundary: out-of-range stencil cells are mirrored (k -> -1-k,
  *     k -> 2^(j+1)-1-k), the even reflection of homogeneous Neumann data;
  *   - detail norm: delta = max_i |d_i| / s_i with s_i = max over leaves |u_i|
@@ -602,35 +602,80 @@ static void leaf_row(const orc_tree *T, int j, const int32_t *k, row_t *r) {
   free(tmp);
 }
 
-int orc_operator(orc_tree *T, int64_t cap, int64_t *rowptr, int32_t *col, double *val, double *rho) {
-  int64_t N = index_leaves(T);
-  int64_t nnz = 0, r = 0;
-  double rmax = 0.0;
-  int32_t k[3];
+/* Rows of the operator, one per leaf in leaf (key) order.  Rows are
+ * independent: with several oracle threads they are built by the
+ * parallel-for in fixed chunks of consecutive leaves, each chunk into its own
+ * buffer, and the chunks are concatenated in order, so the result is that of
+ * the serial loop. */
+typedef struct {
+  const orc_tree *T;
+  const int8_t *lj;     /* level of leaf r */
+  const int32_t *lk;    /* coordinates of leaf r (3 per leaf) */
+  row_t *chunk_rows;    /* per chunk: the concatenated rows */
+  int64_t *cnt;         /* per leaf: entries of its row */
+  double *chunk_rmax;   /* per chunk: largest absolute row sum */
+} op_args;
+
+static void op_rows(void *ctx, int64_t lo, int64_t hi, int c) {
+  op_args *a = (op_args *)ctx;
   row_t row = {0};
-  int over = 0;
-  for (int j = 0; j <= T->J; j++)
-    for (int64_t sm = 0; sm < T->n[j]; sm++) { /* rows in leaf (key) order */
-      orc_key_decode(T->d, (uint64_t)sm | ((uint64_t)j << 48), &(int){0}, k);
-      int64_t p = pos(T, j, k);
-      if (T->lidx[j][p] < 0) continue;
-      row.n = 0;
-      leaf_row(T, j, k, &row);
-      double sa = 0.0;
-      for (int64_t e = 0; e < row.n; e++) {
-        sa += fabs(row.w[e]);
-        if (nnz + e < cap) { col[nnz + e] = row.col[e]; val[nnz + e] = row.w[e]; }
-      }
-      if (nnz + row.n > cap) over = 1;
-      rmax = fmax(rmax, sa);
-      rowptr[T->lidx[j][p]] = nnz;
-      nnz += row.n;
-      r++;
+  row_t *out = &a->chunk_rows[c];
+  double rmax = 0.0;
+  for (int64_t r = lo; r < hi; r++) {
+    row.n = 0;
+    leaf_row(a->T, a->lj[r], a->lk + 3 * r, &row);
+    double sa = 0.0;
+    for (int64_t e = 0; e < row.n; e++) {
+      sa += fabs(row.w[e]);
+      row_add(out, row.col[e], row.w[e]);
     }
-  rowptr[N] = nnz;
-  (void)r;
+    rmax = fmax(rmax, sa);
+    a->cnt[r] = row.n;
+  }
+  a->chunk_rmax[c] = rmax;
   free(row.col);
   free(row.w);
+}
+
+int orc_operator(orc_tree *T, int64_t cap, int64_t *rowptr, int32_t *col, double *val, double *rho) {
+  int64_t N = index_leaves(T);
+  int8_t *lj = malloc(N ? N : 1);
+  int32_t *lk = calloc(3 * (N ? N : 1), sizeof(int32_t));
+  int32_t k[3];
+  for (int j = 0; j <= T->J; j++)
+    for (int64_t sm = 0; sm < T->n[j]; sm++) { /* leaves in key order */
+      orc_key_decode(T->d, (uint64_t)sm | ((uint64_t)j << 48), &(int){0}, k);
+      int32_t r = T->lidx[j][pos(T, j, k)];
+      if (r < 0) continue;
+      lj[r] = (int8_t)j;
+      memcpy(lk + 3 * (int64_t)r, k, sizeof k);
+    }
+  const int64_t chunk = 512, nchunks = (N + chunk - 1) / chunk;
+  op_args a = {T, lj, lk, calloc(nchunks ? nchunks : 1, sizeof(row_t)), malloc(sizeof(int64_t) * (N ? N : 1)),
+               calloc(nchunks ? nchunks : 1, sizeof(double))};
+  orc_parallel_for(N, chunk, op_rows, &a);
+  int64_t nnz = 0;
+  double rmax = 0.0;
+  int over = 0;
+  for (int64_t c = 0; c < nchunks; c++) {
+    const row_t *cr = &a.chunk_rows[c];
+    for (int64_t e = 0; e < cr->n; e++)
+      if (nnz + e < cap) { col[nnz + e] = cr->col[e]; val[nnz + e] = cr->w[e]; }
+    for (int64_t r = c * chunk; r < N && r < (c + 1) * chunk; r++) {
+      rowptr[r] = nnz;
+      nnz += a.cnt[r];
+    }
+    if (nnz > cap) over = 1;
+    rmax = fmax(rmax, a.chunk_rmax[c]);
+    free(cr->col);
+    free(cr->w);
+  }
+  rowptr[N] = nnz;
+  free(a.chunk_rows);
+  free(a.cnt);
+  free(a.chunk_rmax);
+  free(lj);
+  free(lk);
   if (rho) *rho = rmax;
   return over ? -1 : 0;
 }

@@ -9,7 +9,7 @@
  * simplified Newton iterations and embedded error estimation of Hairer and
  * Wanner (Solving ODEs II, Sec. IV.8; cited in the paper as MR1439506).  The
  * steps below restate that description in plain code; every control constant
- * is listed in the comment of orc_radau5 and in the design notes.
+ * is listed in the comment of orc_radau5.
  *
  * Unlike the GPU path (which solves the transformed real + complex m x m
  * systems), the oracle solves the untransformed 3m x 3m simplified-Newton
@@ -348,7 +348,7 @@ static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x >
  * Integrate y' = f(y) from 0 to tend, in place.  hfix > 0 selects the pinned
  * fixed-step mode (every step accepted, no error control); otherwise adaptive.
  *
- * Control (restating Hairer-Wanner IV.8; readings in the design notes):
+ * Control (restating Hairer-Wanner IV.8, where the paper is silent):
  *   tolerances: rtol' = 0.1 rtol^(2/3), atol' = rtol' atol/rtol
  *   Newton:     kappa*Tol = fnewt = max(10 u/rtol', min(0.03, sqrt(rtol'))),
  *               at most kmax = 7 iterations, increment measured as

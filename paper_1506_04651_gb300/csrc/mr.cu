@@ -167,6 +167,7 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
       graded = graded && idx[o] >= 0;
     }
     double dmax = 0.0;
+    bool finite = true;  // fmax drops a NaN operand, so non-finite details are caught here
     if (!graded) {
       dmax = __longlong_as_double(0x7ff8000000000000ll);  // a stencil cell is missing: NaN
     } else {
@@ -176,10 +177,11 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
 #pragma unroll
         for (int o = 0; o < NST; o++) p = __dadd_rn(p, __dmul_rn(sw[parity][o], Vi[idx[o]]));
         double dd = fabs(__dadd_rn(Vi[n], -p)) / scale[i];
+        finite = finite && isfinite(dd);
         dmax = fmax(dmax, dd);
       }
     }
-    if (isnan(dmax)) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
+    if (isnan(dmax) || !finite) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
     tag[n] = dmax >= eps_j[j];
     if (delta_out) delta_out[n] = dmax;
   }
@@ -1028,7 +1030,7 @@ mr_status adapt(mr_ctx* c, double eta) {
   MR_CUDA(c, cudaGetLastError());
   MR_TRY(sync_counts(c));
   if (c->hc.status) {
-    c->last_error = "adaptation met a missing prediction stencil";
+    c->last_error = "adaptation: a detail is not finite (NaN or infinity in the state) or a prediction stencil is missing";
     return (mr_status)c->hc.status;
   }
   c->cur = dst;

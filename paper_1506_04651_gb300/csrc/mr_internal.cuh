@@ -100,7 +100,8 @@ struct DevCounters {
   int irr_rows;
   long long irr_nnz;
   int nleaves;
-  int work_next;                // Radau5 work queue head
+  unsigned long long work_next; // Radau5 work queue head (64-bit: every resident thread takes one
+                                // ticket past the end, which must not wrap near 2^31 cells)
   int overflow;                 // irregular row exceeded its local capacity
   int nretry;                   // rows left to the full-size row builder
 };

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
   double dynold = 0.0, hfac_fail = 0.5, isc[M];
   double gi = 0.0, ai_ = 0.0, bi_ = 0.0;
   CellCount n = {0, 0, 0, 0, 0, 0, 0};
-  int cell = -1;
+  int64_t cell = -1;
   enum { P_TOP, P_FACTOR, P_START, P_NEWTON };
   int phase = P_TOP;
 
@@ -278,11 +278,11 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
     int st = MR_OK;
     bool finish = false;
     if (cell < 0) {
-      cell = atomicAdd(&dc->work_next, 1);
-      if (cell >= N) break;
+      const unsigned long long ticket = atomicAdd(&dc->work_next, 1ull);
+      if (ticket >= (unsigned long long)N) break;
       // finest leaves first: leaves are stored level-major, and the finest
       // levels hold the front cells that need the most steps
-      cell = (int)(N - 1 - cell);
+      cell = N - 1 - (int64_t)ticket;
       if (B.inst) {
         int lo = 0, hi = B.n - 1;  // last instance with offs[b] <= cell
         while (lo < hi) {
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
         Ub = I.U;
         capLb = I.capL;
         cxb = I.complexity;
-        cell -= (int)B.offs[lo];
+        cell -= B.offs[lo];
       }
 #pragma unroll
       for (int i = 0; i < M; i++) y[i] = Ub[i * capLb + cell];
@@ -320,8 +320,15 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
       mdl.rhs(y, f0);
       n.nfev++;
       phase = P_TOP;
+      bool fin = true;
+#pragma unroll
+      for (int i = 0; i < M; i++) fin = fin && isfinite(y[i]);
+      if (!fin) {  // a non-finite state: reported at once, the cell left as it is
+        st = MR_ENONFINITE;
+        finish = true;
+      }
     }
-    if (phase == P_TOP) {
+    if (!finish && phase == P_TOP) {
       if (need_jac) {
         mdl.jac(y, J);
         n.njac++;
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
       }
       phase = P_FACTOR;
     }
-    if (phase == P_FACTOR) {
+    if (!finish && phase == P_FACTOR) {
       if (t + 1.0001 * h >= tend) {
         h = tend - t;
         last = true;
@@ -789,7 +796,7 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   if (c->prob.model == MR_MODEL_IONIC) return react_ionic(c, C, dt);
   MR_CUDA(c, cudaMemsetAsync(c->dc->radau, 0, sizeof(c->dc->radau), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
-  MR_CUDA(c, cudaMemsetAsync(&c->dc->work_next, 0, sizeof(int), c->stream));
+  MR_CUDA(c, cudaMemsetAsync(&c->dc->work_next, 0, sizeof(c->dc->work_next), c->stream));
   // persistent grid: exactly the blocks that are co-resident, each thread
   // pulling cells from the queue until it is empty
   int dev = 0, nsm = 152, per_sm = 1;
@@ -953,6 +960,11 @@ namespace {
 constexpr int kNoallocScratchBytes = 512;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 static_assert(sizeof(DevCounters) <= kNoallocScratchBytes, "scratch too small for the counters");
+// the queue head is drawn once per cell and once more by every resident
+// thread after the last cell; 64 bits keep that from wrapping at any n up to
+// MR_NOALLOC_MAX_CELLS
+static_assert(sizeof(DevCounters::work_next) == 8 && MR_NOALLOC_MAX_CELLS < (1LL << 40),
+              "the Radau5 queue head must not wrap");
 std::mutex g_noalloc_mu;
 constexpr int kNoallocMaxDevices = 256;
 void* g_noalloc_addr[kNoallocMaxDevices] = {};

@@ -563,10 +563,11 @@ __global__ void __launch_bounds__(kTeamBlock, 3)
     int st = MR_OK;
     bool finish = false;
     if (cell < 0) {
-      long long c0 = 0;
-      if (t == 0) c0 = atomicAdd(&dc->work_next, 1);
-      cell = __shfl_sync(mask, c0, 0, TW);
-      if (cell >= ncell) break;
+      unsigned long long c0 = 0;
+      if (t == 0) c0 = atomicAdd(&dc->work_next, 1ull);
+      c0 = __shfl_sync(mask, c0, 0, TW);
+      if (c0 >= (unsigned long long)ncell) break;
+      cell = (int64_t)c0;
       y = real_species ? U[t * capL + cell] : 0.0;
       n = CellCount{0, 0, 0, 0, 0, 0, 0};
       t_ = 0.0;
@@ -587,8 +588,12 @@ __global__ void __launch_bounds__(kTeamBlock, 3)
       f0 = M.rhs(y);
       n.nfev++;
       phase = P_TOP;
+      if (!__all_sync(mask, isfinite(y))) {  // a non-finite state: reported at once, the cell left as it is
+        st = MR_ENONFINITE;
+        finish = true;
+      }
     }
-    if (phase == P_TOP) {
+    if (!finish && phase == P_TOP) {
       if (need_jac) {
         M.jac(y, f0, Jrow, sJt);
         n.njac++;
@@ -597,7 +602,7 @@ __global__ void __launch_bounds__(kTeamBlock, 3)
       }
       phase = P_FACTOR;
     }
-    if (phase == P_FACTOR) {
+    if (!finish && phase == P_FACTOR) {
       if (t_ + 1.0001 * h >= tend) {
         h = tend - t_;
         last = true;
@@ -844,7 +849,7 @@ mr_status launch_team(mr_ctx* c, const typename TM::Params& Pm, const RadauC& C,
   const int64_t N = tb.nleaves;
   MR_CUDA(c, cudaMemsetAsync(c->dc->radau, 0, sizeof(c->dc->radau), c->stream));
   MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
-  MR_CUDA(c, cudaMemsetAsync(&c->dc->work_next, 0, sizeof(int), c->stream));
+  MR_CUDA(c, cudaMemsetAsync(&c->dc->work_next, 0, sizeof(c->dc->work_next), c->stream));
   int dev = 0, nsm = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -4,7 +4,7 @@ This module only generates input data (initial states on the finest grid and
 random instance parameters).  It holds none of the method's arithmetic and is
 the one piece of code that both the GPU path's callers and the oracle's tests
 use.  The paper prints no initial data (Sec. 4 shows BZ fronts, Fig. 3), so
-the recipes below are the ones stated in the design notes:
+these recipes are readings of its figures and of the workload descriptions:
 
 * a tanh front of width w in b = u2 between the rest state b_r and an excited
   value b_e, c = u3 = b, and a = u1 slaved to the fast manifold a = f c/(q + b);
@@ -22,6 +22,10 @@ import numpy as np
 
 BZ_DEFAULT = dict(eps=1e-2, mu=1e-5, f=1.6, q=2e-3)
 BZ_D = (2.5e-3, 2.5e-3, 1.5e-3)
+# front width and position-noise amplitude of the adaptive 2D J = 10 workload
+# (two crossing fronts, eta = 1e-3): sharper and more convoluted fronts than
+# the 3D sphere's, so that 10-20% of the finest cells are leaves
+CROSS_J10 = dict(w=0.01, amp=0.3)
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 

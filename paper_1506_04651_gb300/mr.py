@@ -18,6 +18,7 @@ MR_MODEL_BZ, MR_MODEL_NAGUMO, MR_MODEL_NETWORK, MR_MODEL_IONIC = 1, 2, 3, 4
 IONIC_SPECIES = 21
 MR_FP64, MR_MIXED = 0, 1
 MAX_SPECIES, MAX_LEVEL = 32, 16
+NOALLOC_MAX_CELLS = 2147483647  # MR_NOALLOC_MAX_CELLS of include/mr.h
 
 STATUS = {0: "MR_OK", -1: "MR_EINVAL", -2: "MR_ENOMEM", -3: "MR_ECUDA", -4: "MR_ESTATE",
           -10: "MR_ERADAU_HMIN", -11: "MR_ERADAU_MAXSTEPS", -12: "MR_ERADAU_SINGULAR",

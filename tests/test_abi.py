@@ -64,3 +64,20 @@ def test_rock4_coefficients_match_oracle(native, s):
         np.testing.assert_allclose(g[k], o[k], rtol=2e-12, atol=1e-15)
     np.testing.assert_allclose(g["w"], o["w"], rtol=2e-12)
     np.testing.assert_allclose(g["errc"], o["errc"], rtol=1e-10)
+
+
+def test_noalloc_maximum_rejected_before_gpu_work(native):
+    """The allocation-free reaction rejects one cell more than its documented
+    maximum before touching the device (the buffer is a host array of four
+    doubles, never read)."""
+    src = open(os.path.join(ROOT, "include", "mr.h")).read()
+    mx = int(re.search(r"#define MR_NOALLOC_MAX_CELLS (\d+)LL", src).group(1))
+    assert mx == native.NOALLOC_MAX_CELLS
+    f = native.lib().mr_react_radau5_noalloc
+    f.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p, C.c_int64, C.c_int64,
+                  C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    params = (C.c_double * 4)(1e-2, 1e-5, 1.6, 2e-3)
+    buf = (C.c_double * 4)()
+    assert f(1, params, 4, C.addressof(buf), mx + 1, mx + 1, 5e-4, 1e-6, 1e-6, None, None) == -1
+    assert f(1, params, 4, C.addressof(buf), -1, 4, 5e-4, 1e-6, 1e-6, None, None) == -1

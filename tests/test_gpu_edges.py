@@ -8,6 +8,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_1506_04651_gb300 import inputs as I
+from tests import gridcmp as G
 
 pytestmark = pytest.mark.gpu
 
@@ -98,10 +99,9 @@ def test_nagumo_mixed_form(mr):
         c.strang(1e-2, eta)
     k_o, v_o = T.leaves()
     k_g, v_g = c.leaves()
-    if np.array_equal(k_o, k_g):
-        lev = (k_o >> np.uint64(48)).astype(np.int64)
-        vol = np.ldexp(1.0, -2 * lev)
-        assert np.sum(vol * np.abs(v_g[0] - v_o[0])) / np.sum(vol * np.abs(v_o[0])) <= 1e-5
+    # the mixed form may round a detail to the other side of its threshold,
+    # so the two grids are compared on the finest grid by injection
+    assert G.rel_l1_finest(k_g, v_g, k_o, v_o, 2, J) <= 1e-5
 
 
 def test_step_arguments_rejected(mr):

@@ -25,7 +25,7 @@ def rel_linf(a, b):
 
 
 @pytest.mark.parametrize("d,J,eta,gen", [
-    (2, 10, 1e-3, lambda J: I.bz_cross_2d(J, 2, w=0.01, amp=0.1)),
+    (2, 10, 1e-3, lambda J: I.bz_cross_2d(J, 2, **I.CROSS_J10)),
     (3, 7, 1e-2, lambda J: I.bz_sphere_3d(J, 3)),
 ])
 def test_full_size_build_and_step(mr, d, J, eta, gen):

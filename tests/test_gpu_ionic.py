@@ -28,6 +28,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_1506_04651_gb300 import inputs as I
+from tests import gridcmp as G
 
 pytestmark = pytest.mark.gpu
 
@@ -125,13 +126,17 @@ def test_mixed_form(mr):
         c.strang(1e-3, 1e-3)
     k_o, v_o = T.leaves()
     k_g, v_g = c.leaves()
-    if np.array_equal(k_o, k_g):
-        lev = (k_o >> np.uint64(48)).astype(np.int64)
-        vol = np.ldexp(1.0, -2 * lev)
-        for i in range(21):
-            den = np.sum(vol * np.abs(v_o[i]))
-            if den > 0:
-                assert np.sum(vol * np.abs(v_g[i] - v_o[i])) / den <= 1e-5
+    # compared on the finest grid by injection (the mixed form may adapt
+    # differently where a detail lies within FP32 noise of its threshold);
+    # every species with a non-zero integral
+    A, B = G.finest(k_g, v_g, d, J), G.finest(k_o, v_o, d, J)
+    checked = 0
+    for i in range(21):
+        den = np.sum(np.abs(B[i]))
+        if den > 0:
+            assert np.sum(np.abs(A[i] - B[i])) / den <= 1e-5, i
+            checked += 1
+    assert checked >= 20
 
 
 def test_full_size_step(mr):

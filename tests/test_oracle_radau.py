@@ -173,3 +173,31 @@ def test_bz_jacobian_eigenvalues_reach_order_1e5():
         assert rc == 0
     order = GOLD["bz_jacobian_eigenvalue_order"]["order"]
     assert order / 10 <= big <= order * 10
+
+
+def test_singular_newton_matrix_halves_the_step_and_recovers():
+    """y' = k y with k = gam / tend: on the first attempt (h = tend) the
+    filtering matrix gam/h - k of the error estimate is exactly zero, so the
+    factorisation fails; the step is halved and the integration goes on to
+    the exact solution e^(k tend) within its tolerance."""
+    gam = O.radau_constants()["gam"]
+    tend = 1.0
+    k = gam / tend
+    md = O.make_model("linear", K=[[k]])
+    y, rc, st = O.radau5(md, [1.0], tend, rtol=1e-8, atol=1e-8)
+    assert rc == 0
+    assert abs(y[0] - np.exp(k * tend)) <= 1e-5 * np.exp(k * tend)
+    assert st["status"] == 0 and st["naccept"] > 0
+
+
+def test_six_singular_matrices_in_a_row_are_reported():
+    """K = diag(gam/tend * 2^q), q = 0..5: every halving of h makes the next
+    diagonal entry of gam/h - K exactly zero, so the sixth consecutive
+    singular factorisation ends the integration with MR_ERADAU_SINGULAR."""
+    gam = O.radau_constants()["gam"]
+    tend = 1.0
+    K = np.diag([(gam / tend) * 2.0 ** q for q in range(6)])
+    md = O.make_model("linear", K=K)
+    _, rc, st = O.radau5(md, np.ones(6), tend)
+    assert rc == -12
+    assert st["ndec"] == 6 and st["nstep"] == 0

@@ -67,7 +67,7 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
     f = _entry(mr)
     params = (C.c_double * 4)(1e-2, 1e-5, 1.6, 2e-3)
     buf = torch.zeros(3, 4, dtype=torch.float64, device="cuda")
-    too_many = (1 << 31)
+    too_many = mr.NOALLOC_MAX_CELLS + 1
     assert f(1, params, 4, buf.data_ptr(), too_many, too_many, 5e-4, 1e-6, 1e-6, None, None) == -1
     assert f(1, params, 4, buf.data_ptr(), 4, 3, 5e-4, 1e-6, 1e-6, None, None) == -1  # ld < n
     assert f(7, params, 4, buf.data_ptr(), 4, 4, 5e-4, 1e-6, 1e-6, None, None) == -1  # unknown model
