@@ -120,14 +120,19 @@ typedef struct {
   int64_t kernel_launches;        /* cumulative kernels launched by this context */
   /* cumulative since mr_create, from CUDA events around each launch on the
    * context stream: the Radau5 kernel and the ROCK4 sweep kernel, with their
-   * algorithmic work (Radau5: FP64 operations of the source per counted
-   * event -- BZ: right-hand side 13, Jacobian 10, factorisations 114, Newton
-   * iteration 271, step attempt 246; ROCK4: bytes each sweep must move at
-   * least) */
+   * algorithmic work (Radau5: FP64 operations counted from the kernel's
+   * source per counted event, applied to radau_counters as a lower bound --
+   * for BZ (m = 3): right-hand side 13, Jacobian 10, factorisations 110,
+   * Newton iteration 249 plus 6 for its contraction monitor from the second
+   * iteration on, step attempt 73, extrapolated starting values 142,
+   * accepted step 77; ROCK4: bytes each sweep must move at least) */
   double radau_kernel_ms, radau_alg_flops;
   int64_t radau_kernel_launches;
   double rock_kernel_ms, rock_alg_bytes;
   int64_t rock_kernel_launches;
+  /* cumulative Radau5 counters since mr_create: f evaluations, Jacobians, step
+   * attempts, accepted, rejected, Newton iterations, factorisations, cells */
+  int64_t radau_counters[8];
 } mr_stats;
 
 /* Create a context for `prob` on `cuda_stream` (a cudaStream_t or NULL).

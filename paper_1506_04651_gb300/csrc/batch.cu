@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "mr_internal.cuh"
+#include "radau_common.cuh"
 
 namespace mrg {
 namespace {
@@ -170,11 +171,10 @@ mr_status react_all(mr_batch* b, double dt, double rtol, double atol) {
   S.radau_reject += cnt[4];
   S.radau_newton += cnt[5];
   S.radau_dec += cnt[6];
-  // algorithmic FP64 operations per counted event (as for one context)
-  const bool bz = b->ctx[0]->prob.model == MR_MODEL_BZ;
-  S.radau_alg_flops += (bz ? 13 : 4) * (double)cnt[0] + (bz ? 10 : 4) * (double)cnt[1] +
-                       (bz ? 114 : 6) * (double)cnt[6] + (bz ? 271 : 30) * (double)cnt[5] +
-                       (bz ? 246 : 40) * (double)cnt[2];
+  // algorithmic FP64 operations (radau_work: counted from the kernel's source)
+  int64_t cells = 0;
+  for (mr_ctx* c : b->ctx) cells += c->tb[c->cur].nleaves;
+  S.radau_alg_flops += radau_alg_flops(radau_work(b->ctx[0]->prob.model, b->ctx[0]->m), cnt, cells);
   return MR_OK;
 }
 

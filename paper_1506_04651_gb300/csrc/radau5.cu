@@ -636,6 +636,36 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
 }
 
 // ------------------------------------------------------------ host constants
+}  // namespace
+
+RadauWork radau_work(int model, int M) {
+  const double m = M;
+  const double lu_real = m + m * (m - 1) / 2 + m * (m - 1) * (2 * m - 1) / 3;
+  const double lu_cplx = m * (m + 1) / 2 + 6 * m + 3 * m * (m - 1) + 4 * m * (m - 1) * (2 * m - 1) / 3;
+  const double sol_real = m + 2 * m * (m - 1);
+  RadauWork w;
+  // BZ: r_a 6, r_b 6, r_c 1; J 2 + 1 + 1 + 2 + 4.  NAGUMO: k y y (1 - y) 4;
+  // k (2 y - 3 y y) 5
+  w.rhs = model == MR_MODEL_BZ ? 13 : 4;
+  w.jac = model == MR_MODEL_BZ ? 10 : 5;
+  w.dec = 6 + 2 * m + lu_real + lu_cplx;
+  w.newton = 62 * m + 10 * m * (m - 1) + 3;
+  w.monitor = 6;
+  w.attempt = 19 + 18 * m;
+  w.extrap = 88 + 18 * m;
+  w.accept = (5 + 13 * m + sol_real) + 4 + (11 + m);
+  return w;
+}
+
+double radau_alg_flops(const RadauWork& w, const unsigned long long* cnt, int64_t ncells) {
+  const double fev = cnt[0], jac = cnt[1], nstep = cnt[2], nacc = cnt[3], nrej = cnt[4], nnew = cnt[5],
+               ndec = cnt[6];
+  const double extrap = std::max(0.0, nstep - (double)ncells - nrej);
+  return w.rhs * fev + w.jac * jac + w.dec * ndec + w.newton * nnew + w.monitor * std::max(0.0, nnew - nstep) +
+         w.attempt * nstep + w.extrap * extrap + w.accept * nacc;
+}
+
+namespace {
 void inv3(const double* a, double* r) {
   double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
                a[2] * (a[3] * a[7] - a[4] * a[6]);
@@ -836,15 +866,10 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]);
   s.radau_kernel_ms += ms;
   s.radau_kernel_launches++;
-  // algorithmic FP64 operations, counted from the source of radau_cell per
-  // event (BZ, m = 3): right-hand side 13, Jacobian 10, forming and
-  // factorising the real and complex matrices 114, one Newton iteration
-  // without its three right-hand sides 271, one step attempt (starting values,
-  // transforms, error estimate, step control) 246
-  const bool bz = c->prob.model == MR_MODEL_BZ;
-  const double Ff = bz ? 13 : 4, Fj = bz ? 10 : 4, Fd = bz ? 114 : 6, Fn = bz ? 271 : 30, Fs = bz ? 246 : 40;
-  s.radau_alg_flops += Ff * c->hc.radau[0] + Fj * c->hc.radau[1] + Fd * c->hc.radau[6] + Fn * c->hc.radau[5] +
-                       Fs * c->hc.radau[2];
+  // algorithmic FP64 operations (radau_work: counted from this kernel's source)
+  s.radau_alg_flops += radau_alg_flops(radau_work(c->prob.model, c->m), c->hc.radau, N);
+  for (int q = 0; q < 7; q++) s.radau_counters[q] += (int64_t)c->hc.radau[q];
+  s.radau_counters[7] += N;
   s.radau_fev = c->hc.radau[0];
   s.radau_jac = c->hc.radau[1];
   s.radau_steps = c->hc.radau[2];

@@ -897,6 +897,8 @@ void add_team_flops(mr_ctx* c, double Ff, double Fj) {
   const double Fd = 3 * m * m + (10.0 / 3.0) * m * m * m, Fn = 10 * m * m + 50 * m, Fs = 2 * m * m + 40 * m;
   c->stats.radau_alg_flops += Ff * c->hc.radau[0] + Fj * c->hc.radau[1] + Fd * c->hc.radau[6] +
                               Fn * c->hc.radau[5] + Fs * c->hc.radau[2];
+  for (int q = 0; q < 7; q++) c->stats.radau_counters[q] += (int64_t)c->hc.radau[q];
+  c->stats.radau_counters[7] += c->tb[c->cur].nleaves;
 }
 
 }  // namespace

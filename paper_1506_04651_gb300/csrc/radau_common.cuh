@@ -45,6 +45,42 @@ __device__ inline double pow08(double x) {
 // kernel-side constants from radau_constants' array (tolerances unset)
 RadauC constants_from(const double* rc);
 
+// Algorithmic FP64 work of k_radau (one thread per cell, m = M species),
+// counted operation by operation from its source: every addition,
+// subtraction, multiplication, division and square root is one operation,
+// a*b + c is two whether or not it is fused, and fabs, fmin, fmax,
+// comparisons and negations are none.  Per event:
+//   rhs, jac   one right-hand side, one Jacobian (model-specific)
+//   dec        forming gam/h I - J and (alp + i bet)/h I - J and factorising
+//              them: 6 + 2M + LU_real(M) + LU_cplx(M), where
+//              LU_real = M + M(M-1)/2 + M(M-1)(2M-1)/3 and
+//              LU_cplx = M(M+1)/2 + 6M + 3M(M-1) + 4M(M-1)(2M-1)/3
+//   newton     one simplified Newton iteration without its three right-hand
+//              sides: stage arguments 3M, T^-1 F 15M, residuals 10M, real
+//              solve M + 2M(M-1), complex solve 6M + 8M(M-1), increment norm
+//              9M + 2, W update 3M, Z = T W 15M, stopping test 1
+//              = 62M + 10M(M-1) + 3
+//   monitor    contraction rate and its test (iterations k >= 2): 6
+//   attempt    every step attempt: step-size floor 2, W = T^-1 Z 15M, scales
+//              3M, faccon^0.8 14, shifted eigenvalues 3 = 19 + 18M
+//   extrap     starting values extrapolated from the last accepted step:
+//              1 + 3 (2 + 27 + 6M) = 88 + 18M
+//   accept     error estimate 5 + 13M + solve_real(M), step-size factor 4,
+//              accepted-step control, update and time 11 + M
+// A launch's work is taken as the lower bound
+//   rhs nfev + jac njac + dec ndec + newton nnewton + monitor (nnewton - nstep)
+//   + attempt nstep + extrap max(0, nstep - ncells - nreject) + accept naccept
+// (an attempt extrapolates unless it precedes its cell's first accepted
+// step, so at least nstep - ncells - nreject attempts do; error estimates of
+// rejected steps and the refiltered estimate are left out).
+struct RadauWork {
+  double rhs, jac, dec, newton, monitor, attempt, extrap, accept;
+};
+RadauWork radau_work(int model, int M);
+// counters in the order of DevCounters::radau (fev, jac, steps, accept,
+// reject, newton, dec)
+double radau_alg_flops(const RadauWork& w, const unsigned long long* cnt, int64_t ncells);
+
 // Reaction sub-steps of the network and membrane models (team kernels); C
 // carries the transformed tolerances of the call.
 mr_status react_network(mr_ctx* c, const RadauC& C, double dt);

@@ -127,6 +127,19 @@ def bz_sphere_3d(J: int, seed: int, r0: float = 0.3, w: float = 0.02,
     return bz_state(b, b.copy(), f, q)
 
 
+NAGUMO_K, NAGUMO_D = 10.0, 0.1  # Sec. 1 item I: k = 10, diffusion 0.1
+
+
+def nagumo_front(d: int, J: int, r0: float = 0.3, k: float = NAGUMO_K, D: float = NAGUMO_D):
+    """A circular (2D) or spherical (3D) NAGUMO front of radius r0 about the
+    domain centre with the travelling-front profile 1 / (1 + exp(lam (r - r0))),
+    lam = sqrt(k / (2 D)); values in [0, 1].  Shape (1, 2^(dJ))."""
+    xs = cell_centres(d, J)
+    r = np.sqrt(sum((x - 0.5) ** 2 for x in xs))
+    lam = np.sqrt(k / (2.0 * D))
+    return (1.0 / (1.0 + np.exp(lam * (r - r0)))).reshape(1, -1)
+
+
 def batch_instances(n: int, master_seed: int = 2026):
     """Per-instance parameters of the batched workload: J ~ U{7..10}, f ~ U[0.9, 2.0],
     eta log-uniform in [1e-4, 1e-2], front position ~ U[0.2, 0.8]."""

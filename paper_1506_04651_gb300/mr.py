@@ -46,13 +46,13 @@ class Stats(C.Structure):
                 ("radau_kernel_ms", C.c_double), ("radau_alg_flops", C.c_double),
                 ("radau_kernel_launches", C.c_int64),
                 ("rock_kernel_ms", C.c_double), ("rock_alg_bytes", C.c_double),
-                ("rock_kernel_launches", C.c_int64)]
+                ("rock_kernel_launches", C.c_int64), ("radau_counters", C.c_int64 * 8)]
 
     def as_dict(self):
         out = {}
         for name, _ in self._fields_:
             v = getattr(self, name)
-            out[name] = list(v) if name == "leaves_per_level" else v
+            out[name] = list(v) if name in ("leaves_per_level", "radau_counters") else v
         return out
 
 

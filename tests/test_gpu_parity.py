@@ -240,3 +240,25 @@ def test_nagumo_model_parity(mr):
     k_g, v_g = ctx.leaves()
     assert np.array_equal(k_o, k_g)
     assert rel_linf(v_g, v_o) <= 1e-9
+
+
+@pytest.mark.parametrize("d,J,eta", [(3, 6, 1e-3), (2, 9, 1e-4)])
+def test_nagumo_front_trajectory_matches_oracle(mr, d, J, eta):
+    """NAGUMO (Sec. 1 item I: k = 10, diffusion 0.1, dt = 1e-2) from the
+    travelling-front profile of a sphere / circle of radius 0.3, the bench's
+    adaptation-heavy workload at a smaller finest level: the grids equal the
+    oracle's after each of five steps and the values agree to 1e-9."""
+    md = O.make_model("nagumo", params=(I.NAGUMO_K,))
+    u0 = I.nagumo_front(d, J)
+    T = O.Tree(d, J, 1, jmin=2)
+    T.set_full(u0)
+    assert T.adapt(eta) == 0
+    ctx = gpu_ctx(mr, d, J, model="nagumo")
+    ctx.build(u0, eta)
+    for s in range(5):
+        assert T.strang(md, [I.NAGUMO_D], 1e-2, eta) == 0
+        ctx.strang(1e-2, eta)
+        k_o, v_o = T.leaves()
+        k_g, v_g = ctx.leaves()
+        assert np.array_equal(k_o, k_g), s
+        assert rel_linf(v_g, v_o) <= 1e-9 * (s + 1), s
