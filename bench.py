@@ -58,6 +58,14 @@ WORKLOADS = {
                             desc="3D BZ, J=9 (512^3 finest, 134M cells), eta=1e-2, spherical front r=0.3, "
                                  "w=0.02 + smooth seeded noise, dt=1e-3, FP64: the HBM-resident point of the "
                                  "3D BZ workload (leaf vectors larger than L2)"),
+    "nagumo2d_J10_eta1e-4": dict(d=2, J=10, eta=1e-4, dt=1e-2, gen="nagumo", seed=0, model="nagumo",
+                                 desc="2D NAGUMO (k=10, diffusion 0.1), J=10 (1024^2 finest), eta=1e-4, circular "
+                                      "front of radius 0.3 with the travelling-front profile, dt=1e-2, FP64: "
+                                      "a cheap, non-stiff reaction, so the adaptation's share of the step is "
+                                      "large (the paper's Table 3 case)"),
+    "nagumo3d_J8_eta1e-3": dict(d=3, J=8, eta=1e-3, dt=1e-2, gen="nagumo", seed=0, model="nagumo", oracle_J=6,
+                                desc="3D NAGUMO (k=10, diffusion 0.1), J=8 (256^3 finest), eta=1e-3, spherical "
+                                     "front of radius 0.3 with the travelling-front profile, dt=1e-2, FP64"),
     "net3d_J8_eta1e-3": dict(d=3, J=8, eta=1e-3, dt=1e-3, gen="network", seed=5, model="network",
                              oracle_J=4,
                              desc="3D stiff mass-action network, 16 species, 32 reversible reactions "
@@ -86,6 +94,8 @@ def initial_state(w, J=None):
     J = J or w["J"]
     if w["gen"] == "network":
         return I.network_bumps(w["d"], J, w["seed"])
+    if w["gen"] == "nagumo":
+        return I.nagumo_front(w["d"], J)
     if w["gen"] == "ionic":
         return I.ionic_core(w["d"], J, w["seed"])
     if w["gen"] == "cross":
@@ -106,6 +116,9 @@ def make_context(mr, w, stream, precision=0):
     if w.get("model") == "ionic":
         return mr.Context(mr.problem(w["d"], w["J"], model="ionic", D=I.IONIC_D, precision=precision),
                           stream=stream)
+    if w.get("model") == "nagumo":
+        return mr.Context(mr.problem(w["d"], w["J"], model="nagumo", params=(I.NAGUMO_K,), D=(I.NAGUMO_D,),
+                                     precision=precision), stream=stream)
     return mr.Context(mr.problem(w["d"], w["J"], precision=precision), stream=stream)
 
 
@@ -118,6 +131,8 @@ def oracle_model(w):
         return O.make_model("network", m=16, params=(sp, kf, kb)), D, 16
     if w.get("model") == "ionic":
         return O.make_model("ionic"), I.IONIC_D, I.IONIC_M
+    if w.get("model") == "nagumo":
+        return O.make_model("nagumo", params=(I.NAGUMO_K,)), (I.NAGUMO_D,), 1
     return O.make_model("bz"), I.BZ_D, 3
 
 
@@ -250,9 +265,10 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_oracle_rate(w, u0, budget_s=20.0, max_steps=100, threads=1):
-    """The oracle as it stands (single-threaded C), Strang steps on the same
-    workload until the time budget is spent; returns (rate, steps, cores)."""
+def cpu_oracle_rate(w, u0, budget_s=20.0, max_steps=100, threads=1, want_state=False):
+    """The oracle as it stands (C, `threads` threads in its parallel-for),
+    Strang steps on the same workload until the time budget is spent;
+    returns (rate, steps, cores), plus its final leaves when want_state."""
     from oracle import oracle as O
     md, D, m = oracle_model(w)
     J = w.get("oracle_J", w["J"])
@@ -271,7 +287,32 @@ def cpu_oracle_rate(w, u0, budget_s=20.0, max_steps=100, threads=1):
             steps += 1
     finally:
         O.set_threads(1)
+    if want_state:
+        return leaves / t_tot, steps, threads, T.leaves()
     return leaves / t_tot, steps, threads
+
+
+def radau_work(model, m):
+    """FP64 operations per counted event of the one-thread-per-cell Radau5
+    kernel, the closed forms in m counted from its source (include/mr.h,
+    csrc/radau_common.cuh); None for the team-kernel models."""
+    if model not in ("bz", "nagumo"):
+        return None
+    lu_real = m + m * (m - 1) / 2 + m * (m - 1) * (2 * m - 1) / 3
+    lu_cplx = m * (m + 1) / 2 + 6 * m + 3 * m * (m - 1) + 4 * m * (m - 1) * (2 * m - 1) / 3
+    sol_real = m + 2 * m * (m - 1)
+    return {"rhs": 13 if model == "bz" else 4, "jac": 10 if model == "bz" else 5,
+            "dec": 6 + 2 * m + lu_real + lu_cplx, "newton": 62 * m + 10 * m * (m - 1) + 3, "monitor": 6,
+            "attempt": 19 + 18 * m, "extrap": 88 + 18 * m, "accept": (5 + 13 * m + sol_real) + 4 + (11 + m)}
+
+
+def radau_flops(work, cnt):
+    """Lower bound of a run's algorithmic FP64 operations from the Radau5
+    counters (fev, jac, steps, accept, reject, newton, dec, cells)."""
+    fev, jac, nstep, nacc, nrej, nnew, ndec, cells = cnt
+    return (work["rhs"] * fev + work["jac"] * jac + work["dec"] * ndec + work["newton"] * nnew
+            + work["monitor"] * max(0, nnew - nstep) + work["attempt"] * nstep
+            + work["extrap"] * max(0, nstep - cells - nrej) + work["accept"] * nacc)
 
 
 def run_reference(args, w):
@@ -417,7 +458,17 @@ def run_gpu(args, w):
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s",
                  "note": "algorithmic bytes of the sweeps (tables once per sweep, vectors read and written once) "
                          "over the launch time; a roofline only where the leaf vectors exceed L2"}
-    kernels = {"radau": {"ms": rad_ms, "launches": rad_n, "tflops": rad_fl / max(rad_ms, 1e-9) / 1e9},
+    rad_cnt = [b - a for a, b in zip(st0["radau_counters"], st1["radau_counters"])]
+    work = radau_work(w.get("model", "bz"), ctx.m)
+    kernels = {"radau": {"ms": rad_ms, "launches": rad_n, "tflops": rad_fl / max(rad_ms, 1e-9) / 1e9,
+                         "counters": dict(zip(("fev", "jac", "steps", "accept", "reject", "newton", "dec", "cells"),
+                                              rad_cnt)),
+                         "work_per_event": work,
+                         "alg_flops": rad_fl,
+                         "alg_flops_from_counters": radau_flops(work, rad_cnt) if work else None,
+                         "note": "achieved = alg_flops / ms; alg_flops = sum of counters x work_per_event "
+                                 "(lower bound: extrapolated attempts >= steps - cells - reject, error "
+                                 "estimates of accepted steps only)"},
                "rock": {"ms": rock_ms, "launches": rock_n,
                         "gbs": rock_b / max(rock_ms, 1e-9) / 1e6},
                "step_ms": ms / args.steps,
@@ -469,18 +520,34 @@ def run_gpu(args, w):
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(args, w, mr, torch, dev, stream, u0)
+    hbm_point = None
+    if args.workload == DEFAULT and not args.no_hbm_extra and not args.J:
+        hbm_point = run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf)
     if pg:
         pg.barrier()
     if rank != 0:
         ctx.close()
         return
     cpu = None
+    final = mixed.pop("_final") if mixed else None
     if ws == 1 and not args.no_cpu_baseline:
         oj = w.get("oracle_J", w["J"])
         where = ("the same workload" if oj == w["J"] else
                  f"the same problem at finest level J={oj} (the full size takes minutes per oracle step)")
-        rate, steps, cores = cpu_oracle_rate(w, initial_state(w, oj), budget_s=12.0, max_steps=50,
-                                             threads=host_cores())
+        # at full size the oracle runs the same warm-up + timed steps as the
+        # mixed comparison (within a bounded budget), and its final state is
+        # the reference of the mixed and FP64 errors
+        full = oj == w["J"] and final is not None
+        nst = args.warmup + args.steps
+        rate, steps, cores, ostate = cpu_oracle_rate(w, initial_state(w, oj), budget_s=45.0 if full else 12.0,
+                                                     max_steps=nst if full else 50, threads=host_cores(),
+                                                     want_state=True)
+        if full and steps == nst:
+            ko, vo = ostate
+            mixed["rel_l1_vs_fp64_oracle"] = rel_l1_finest(*final["mixed"], ko, vo, w["d"], w["J"])
+            mixed["fp64_path_rel_l1_vs_fp64_oracle"] = rel_l1_finest(*final["fp64"], ko, vo, w["d"], w["J"])
+            mixed["fp64_path_grid_equals_oracle"] = bool(np.array_equal(final["fp64"][0], ko))
+            mixed["oracle_steps"] = steps
         rate1, steps1, _ = cpu_oracle_rate(w, initial_state(w, oj), budget_s=12.0, max_steps=50, threads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {steps} Strang steps of {where} from its initial grid (C oracle, "
@@ -496,7 +563,7 @@ def run_gpu(args, w):
                        "leaves_last_step": st["leaves"], "compression_ratio": st["compression_ratio"],
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roof, "roofline_rock4": roof_rock, "roofline_adapt": roof_adapt, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "mixed": mixed,
+            "gpu_launches": launches, "clocks": clk, "mixed": mixed, "hbm_point": hbm_point,
             "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
     if conservation:
         line["conservation"] = conservation
@@ -507,22 +574,92 @@ def run_gpu(args, w):
 
 
 def finest_grid(keys, vals, d, J):
-    """Leaf values injected piecewise-constant onto the level-J grid."""
-    n = 1 << J
+    """Leaf values injected piecewise-constant onto the level-J grid
+    (lexicographic, x fastest)."""
+    keys = np.asarray(keys, dtype=np.uint64)
     lev = (keys >> np.uint64(48)).astype(np.int64)
     code = (keys & np.uint64((1 << 48) - 1)).astype(np.int64)
-    k = np.zeros((d, len(keys)), dtype=np.int64)
-    for b in range(J):
-        for a in range(d):
-            k[a] |= ((code >> (d * b + (d - 1 - a))) & 1) << b
+    n = 1 << J
     out = np.zeros((vals.shape[0],) + (n,) * d)
     for j in np.unique(lev):
-        sel = lev == j
+        sel = np.nonzero(lev == j)[0]
+        k = np.zeros((d, len(sel)), dtype=np.int64)
+        for b in range(j):
+            for a in range(d):
+                k[a] |= ((code[sel] >> (d * b + (d - 1 - a))) & 1) << b
         bsz = 1 << (J - j)
-        for r in np.nonzero(sel)[0]:
-            sl = tuple(slice(k[a, r] * bsz, (k[a, r] + 1) * bsz) for a in reversed(range(d)))
-            out[(slice(None),) + sl] = vals[:, r][(slice(None),) + (None,) * d]
+        offs = np.arange(bsz)
+        idx = []
+        for a in range(d):
+            shape = [len(sel)] + [1] * d
+            shape[1 + (d - 1 - a)] = bsz
+            idx.append(((k[a] * bsz)[:, None] + offs[None, :]).reshape(shape))
+        for i in range(vals.shape[0]):
+            out[(i,) + tuple(idx[a] for a in reversed(range(d)))] = vals[i, sel].reshape([len(sel)] + [1] * d)
     return out.reshape(vals.shape[0], -1)
+
+
+def rel_l1_finest(ka, va, kb, vb, d, J):
+    """max over species of |a - b|_1 / |b|_1 over the finest grid (b the reference)."""
+    A, B = finest_grid(ka, va, d, J), finest_grid(kb, vb, d, J)
+    return max(float(np.sum(np.abs(A[i] - B[i])) / max(np.sum(np.abs(B[i])), 1e-300)) for i in range(len(B)))
+
+
+def run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf, steps=3, warmup=2):
+    """The HBM-resident point of the 3D BZ workload (J = 9, 512^3 finest,
+    leaf vectors larger than L2) as a bounded extra of the default line: a
+    few CUDA-event-timed steps with the L2 flushed before each, and the
+    rooflines of its ROCK4 sweeps (bytes against HBM) and its adaptation."""
+    w = WORKLOADS["bz3d_J9_eta1e-2"]
+    t0 = time.perf_counter()
+    u0 = torch.from_numpy(initial_state(w)).to(dev)
+    ctx = make_context(mr, w, stream)
+    ctx.build(u0, w["eta"])
+    del u0
+    for _ in range(warmup):
+        ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st0 = ctx.stats()
+    ms, leaves, nodes = 0.0, 0, 0
+    ph = {"adapt_and_tables": 0.0, "react_both_halves": 0.0, "diffuse": 0.0}
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        sk = ctx.stats()
+        leaves += sk["leaves"]
+        nodes += sk["nodes"]
+        ph["adapt_and_tables"] += sk["ms_adapt"]
+        ph["react_both_halves"] += sk["ms_react"]
+        ph["diffuse"] += sk["ms_diffuse"]
+    st1 = ctx.stats()
+    ctx.close()
+    peak = hbm or 6800.0
+    rock_ms = st1["rock_kernel_ms"] - st0["rock_kernel_ms"]
+    rock_b = st1["rock_alg_bytes"] - st0["rock_alg_bytes"]
+    rad_ms = st1["radau_kernel_ms"] - st0["radau_kernel_ms"]
+    rad_fl = st1["radau_alg_flops"] - st0["radau_alg_flops"]
+    adapt_ms = ph["adapt_and_tables"] / steps
+    adapt_b = 2.0 * (nodes / steps) * (8.0 * 3 + 6.0)
+    return {"workload": "bz3d_J9_eta1e-2", "desc": w["desc"], "steps": steps, "warmup": warmup,
+            "value": leaves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "leaves_last_step": st1["leaves"], "irregular_rows": st1["irregular_rows"],
+            "irregular_nnz": st1["irregular_nnz"],
+            "phase_ms_per_step": {k: v / steps for k, v in ph.items()},
+            "roofline_rock4": {"bound": "hbm", "achieved": rock_b / (rock_ms * 1e-3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": rock_b / (rock_ms * 1e-3) / 1e9 / peak,
+                               "ms_per_launch": rock_ms / max(1, st1["rock_kernel_launches"] -
+                                                              st0["rock_kernel_launches"])},
+            "roofline_adapt": {"bound": "hbm", "achieved": adapt_b / (adapt_ms * 1e-3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": adapt_b / (adapt_ms * 1e-3) / 1e9 / peak},
+            "roofline_radau": {"bound": "alu", "achieved": rad_fl / (rad_ms * 1e-3) / 1e12, "peak": fp64_tf,
+                               "unit": "TFLOP/s", "frac": rad_fl / (rad_ms * 1e-3) / 1e12 / fp64_tf},
+            "l2": "flushed before every timed step (256 MB write); state and work vectors exceed L2",
+            "wall_s": time.perf_counter() - t0}
 
 
 def run_mixed(args, w, mr, torch, dev, stream, u0):
@@ -548,17 +685,9 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
         c.close()
     kf, vf = res[mr.MR_FP64][2], res[mr.MR_FP64][3]
     km, vm = res[mr.MR_MIXED][2], res[mr.MR_MIXED][3]
-    if np.array_equal(kf, km):
-        # same grid: the finest-grid L1 norm is the leaf sum weighted by the
-        # number of finest cells each leaf covers
-        vol = np.ldexp(1.0, (w["d"] * (w["J"] - (kf >> np.uint64(48)).astype(np.int64))).astype(np.int32))
-        err = max(float(np.sum(vol * np.abs(vm[i] - vf[i])) / np.sum(vol * np.abs(vf[i]))) for i in range(len(vf)))
-    else:
-        # the two forms adapted differently (a detail at the threshold
-        # rounded to the other side): compared on the finest grid
-        f64 = finest_grid(kf, vf, w["d"], w["J"])
-        mix = finest_grid(km, vm, w["d"], w["J"])
-        err = max(float(np.sum(np.abs(mix[i] - f64[i])) / np.sum(np.abs(f64[i]))) for i in range(len(f64)))
+    # on the finest grid, so that leaves one form refined and the other not
+    # (a detail at the threshold rounded to the other side) still count
+    err = rel_l1_finest(km, vm, kf, vf, w["d"], w["J"]) if w["d"] * w["J"] <= 24 else None
     # the same norm over the leaves both grids share: the arithmetic's part
     # of the difference, without the cells one form refined and the other not
     _, i_f, i_m = np.intersect1d(kf, km, assume_unique=True, return_indices=True)
@@ -573,7 +702,8 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
             "form": "Radau5 Newton factorisations and solves in FP32; ROCK4 stage vectors in FP32; "
                     "Radau5 residuals, both error norms, step control, the state between sub-steps, "
                     "details and mass in FP64",
-            "note": "no L2 flush between these steps; the FP64 path matches the oracle to 1e-9 per step"}
+            "note": "no L2 flush between these steps; the FP64 path matches the oracle to 1e-9 per step",
+            "_final": {"fp64": (kf, vf), "mixed": (km, vm)}}
 
 
 def run_batch(args, b):
@@ -725,6 +855,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCH))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-hbm-extra", action="store_true",
+                    help="skip the HBM-resident 3D J=9 extra of the default workload")
     ap.add_argument("--J", type=int, default=0,
                     help="run the workload at another finest level (profiling captures of a smaller case); "
                          "the line's config records it")
