@@ -547,6 +547,8 @@ def run_gpu(args, w):
             mixed["rel_l1_vs_fp64_oracle"] = rel_l1_finest(*final["mixed"], ko, vo, w["d"], w["J"])
             mixed["fp64_path_rel_l1_vs_fp64_oracle"] = rel_l1_finest(*final["fp64"], ko, vo, w["d"], w["J"])
             mixed["fp64_path_grid_equals_oracle"] = bool(np.array_equal(final["fp64"][0], ko))
+            mixed["f32_details"]["rel_l1_vs_fp64_oracle"] = rel_l1_finest(*final["f32_details"], ko, vo, w["d"],
+                                                                          w["J"])
             mixed["oracle_steps"] = steps
         rate1, steps1, _ = cpu_oracle_rate(w, initial_state(w, oj), budget_s=12.0, max_steps=50, threads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -665,7 +667,7 @@ def run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf, steps=3, warmup=2):
 def run_mixed(args, w, mr, torch, dev, stream, u0):
     nsteps = args.warmup + args.steps
     res = {}
-    for prec in (mr.MR_FP64, mr.MR_MIXED):
+    for prec in (mr.MR_FP64, mr.MR_MIXED, mr.MR_MIXED_F32_DETAILS):
         c = make_context(mr, w, stream, precision=prec)
         c.build(torch.from_numpy(u0).to(dev), w["eta"])
         for _ in range(args.warmup):
@@ -694,6 +696,16 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
     vol_c = np.ldexp(1.0, (w["d"] * (w["J"] - (kf[i_f] >> np.uint64(48)).astype(np.int64))).astype(np.int32))
     err_common = max(float(np.sum(vol_c * np.abs(vm[i][i_m] - vf[i][i_f])) / max(np.sum(vol_c * np.abs(vf[i][i_f])), 1e-300))
                      for i in range(len(vf)))
+    # the option with FP32 details: the cells where its grid and the FP64
+    # path's differ (leaves of one and not the other) are the grid flips
+    kd, vd = res[mr.MR_MIXED_F32_DETAILS][2], res[mr.MR_MIXED_F32_DETAILS][3]
+    f32d = {"value": res[mr.MR_MIXED_F32_DETAILS][0], "ms_per_step": res[mr.MR_MIXED_F32_DETAILS][1],
+            "speedup_vs_fp64": res[mr.MR_MIXED_F32_DETAILS][0] / res[mr.MR_FP64][0],
+            "rel_l1_vs_fp64_path": rel_l1_finest(kd, vd, kf, vf, w["d"], w["J"]) if w["d"] * w["J"] <= 24 else None,
+            "grid_flips_vs_fp64_path": int(len(np.setxor1d(kd, kf, assume_unique=True))),
+            "leaves": int(len(kd)),
+            "form": "as the mixed form, and the MR details predicted and differenced in FP32 from the FP64 "
+                    "node values (thresholds and normalisation in FP64)"}
     return {"value": res[mr.MR_MIXED][0], "ms_per_step": res[mr.MR_MIXED][1],
             "fp64_value_same_run": res[mr.MR_FP64][0], "speedup_vs_fp64": res[mr.MR_MIXED][0] / res[mr.MR_FP64][0],
             "rel_l1_vs_fp64_path": err, "steps": nsteps,
@@ -703,7 +715,8 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
                     "Radau5 residuals, both error norms, step control, the state between sub-steps, "
                     "details and mass in FP64",
             "note": "no L2 flush between these steps; the FP64 path matches the oracle to 1e-9 per step",
-            "_final": {"fp64": (kf, vf), "mixed": (km, vm)}}
+            "f32_details": f32d,
+            "_final": {"fp64": (kf, vf), "mixed": (km, vm), "f32_details": (kd, vd)}}
 
 
 def run_batch(args, b):

@@ -56,7 +56,7 @@ typedef enum {
 } mr_status;
 
 enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2, MR_MODEL_NETWORK = 3, MR_MODEL_IONIC = 4 };
-enum { MR_FP64 = 0, MR_MIXED = 1 };
+enum { MR_FP64 = 0, MR_MIXED = 1, MR_MIXED_F32_DETAILS = 2 };
 
 #define MR_MAX_SPECIES 32
 #define MR_IONIC_SPECIES 21
@@ -94,7 +94,12 @@ enum { MR_FP64 = 0, MR_MIXED = 1 };
  *   precision MR_FP64, or MR_MIXED: Radau5 factorises and solves its Newton
  *             systems in FP32 and the ROCK4 stages run on FP32 vectors
  *             (Radau5 residuals, both error norms, step control, the state
- *             between sub-steps, details and mass stay FP64)
+ *             between sub-steps, details and mass stay FP64), or
+ *             MR_MIXED_F32_DETAILS: MR_MIXED with the MR details (Eq.
+ *             detail) also predicted and differenced in FP32 from the FP64
+ *             node values (thresholds and the normalisation stay FP64); the
+ *             adapted grid may then differ from the FP64 one where a detail
+ *             lies within FP32 rounding of its threshold
  *   max_leaves leaf capacity; 0 means 2^(d J)
  */
 typedef struct {

@@ -233,7 +233,8 @@ mr_status mr_create(const mr_problem* p, void* stream, mr_ctx** out) {
   *out = nullptr;
   if (p->dim < 2 || p->dim > 3 || p->J < 1 || p->J > kMaxL || p->dim * p->J > 30) return MR_EINVAL;
   if (p->jmin < 1 || p->jmin > p->J) return MR_EINVAL;
-  if (p->precision != MR_FP64 && p->precision != MR_MIXED) return MR_EINVAL;
+  if (p->precision != MR_FP64 && p->precision != MR_MIXED && p->precision != MR_MIXED_F32_DETAILS)
+    return MR_EINVAL;
   if (p->model == MR_MODEL_BZ) {
     if (p->m != 3 || p->nparams < 4) return MR_EINVAL;
     if (!(p->params[0] > 0) || !(p->params[1] > 0)) return MR_EINVAL;

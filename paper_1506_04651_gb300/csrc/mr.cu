@@ -122,7 +122,17 @@ __device__ inline double predict(const double* __restrict__ V, const int32_t* __
   return s;
 }
 
-template <int D>
+// round-to-nearest sums and products without contraction, in the detail
+// arithmetic's precision
+__device__ inline double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ inline float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ inline double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+// DT: arithmetic of the prediction and the difference (double, or float in
+// the mixed form with FP32 details: node values rounded to float, weights
+// exact in either); the normalised detail is compared with eps_j in double
+template <int D, typename DT = double>
 __global__ void k_details(const double* __restrict__ V, const uint32_t* __restrict__ code,
                           const uint8_t* __restrict__ lvl, const int32_t* __restrict__ dmap,
                           Level L, int64_t nnodes, int m, int64_t capN, const double* __restrict__ scale,
@@ -131,7 +141,7 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
   // the 3^d prediction weights of each child parity, built in the order
   // predict() multiplies them (they are products of 1 and +-1/8, exact)
   constexpr int NST = D == 2 ? 9 : 27;
-  __shared__ double sw[1 << D][NST];
+  __shared__ DT sw[1 << D][NST];
   for (int q = threadIdx.x; q < (1 << D) * NST; q += blockDim.x) {
     const int par = q / NST;
     int oo = q % NST;
@@ -141,7 +151,7 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
       oo /= 3;
       w = __dmul_rn(w, wpred((par >> a) & 1, off));
     }
-    sw[par][q % NST] = w;
+    sw[par][q % NST] = (DT)w;  // a product of 1 and +-1/8: exact in float too
   }
   __syncthreads();
   for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nnodes;
@@ -173,12 +183,12 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
     } else {
       for (int i = 0; i < m; i++) {
         const double* Vi = V + i * capN;
-        double p = 0.0;  // same products and sums, in the same order, as predict()
+        DT p = DT(0);  // same products and sums, in the same order, as predict()
 #pragma unroll
-        for (int o = 0; o < NST; o++) p = __dadd_rn(p, __dmul_rn(sw[parity][o], Vi[idx[o]]));
-        double dd = fabs(__dadd_rn(Vi[n], -p)) / scale[i];
+        for (int o = 0; o < NST; o++) p = add_rn(p, mul_rn(sw[parity][o], (DT)Vi[idx[o]]));
+        const DT dd = fabs(add_rn((DT)Vi[n], -p)) / (DT)scale[i];
         finite = finite && isfinite(dd);
-        dmax = fmax(dmax, dd);
+        dmax = fmax(dmax, (double)dd);
       }
     }
     if (isnan(dmax) || !finite) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
@@ -987,12 +997,11 @@ mr_status adapt(mr_ctx* c, double eta) {
   if (c->hc.status) return (mr_status)c->hc.status;
   double* dpar = c->red_out;  // small device parameter block
   MR_CUDA(c, cudaMemcpyAsync(dpar, hs, sizeof(double) * (kMaxM + J + 1), cudaMemcpyHostToDevice, c->stream));
-  if (D == 2)
-    k_details<2><<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(
-        c->V, t.code, t.lvl, t.dmap, L, t.nnodes, m, c->cap_nodes, dpar, dpar + kMaxM, c->tag, nullptr, c->dc);
-  else
-    k_details<3><<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(
-        c->V, t.code, t.lvl, t.dmap, L, t.nnodes, m, c->cap_nodes, dpar, dpar + kMaxM, c->tag, nullptr, c->dc);
+  const bool f32d = c->prob.precision == MR_MIXED_F32_DETAILS;
+  const auto details = D == 2 ? (f32d ? k_details<2, float> : k_details<2, double>)
+                              : (f32d ? k_details<3, float> : k_details<3, double>);
+  details<<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(c->V, t.code, t.lvl, t.dmap, L, t.nnodes, m, c->cap_nodes,
+                                                        dpar, dpar + kMaxM, c->tag, nullptr, c->dc);
   c->launches++;
   // flags and the level sweep
   MR_CUDA(c, cudaMemsetAsync(c->fl_state, 0, c->cap_dense_int, c->stream));

@@ -832,7 +832,7 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   int dev = 0, nsm = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const bool mixed = c->prob.precision == MR_MIXED;
+  const bool mixed = c->prob.precision != MR_FP64;
   const void* kern = c->prob.model == MR_MODEL_BZ
                          ? (mixed ? (const void*)k_radau<BZ, float> : (const void*)k_radau<BZ, double>)
                          : (mixed ? (const void*)k_radau<Nagumo, float> : (const void*)k_radau<Nagumo, double>);
@@ -948,7 +948,7 @@ mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double a
           cudaSuccess)
     return MR_ECUDA;
   mr_status st;
-  const bool mixed = prec == MR_MIXED;
+  const bool mixed = prec != MR_FP64;
   if (model == MR_MODEL_BZ) {
     std::vector<BZ> mds(n);
     for (int b = 0; b < n; b++) {

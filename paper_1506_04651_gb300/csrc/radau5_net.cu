@@ -853,7 +853,7 @@ mr_status launch_team(mr_ctx* c, const typename TM::Params& Pm, const RadauC& C,
   int dev = 0, nsm = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const bool mixed = c->prob.precision == MR_MIXED;
+  const bool mixed = c->prob.precision != MR_FP64;
   const void* kern = mixed ? (const void*)k_radau_team<TM, float> : (const void*)k_radau_team<TM, double>;
   const size_t smem = mixed ? team_smem<TM, float>() : team_smem<TM, double>();
   MR_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1410,7 +1410,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   // kernel are marked done); more species run in windows of 16
   const int M = m == 1 ? 1 : (m == 3 ? 3 : 16);
   // FP64 stage vectors, or FP32 in the mixed form
-  const bool f32 = c->prob.precision == MR_MIXED;
+  const bool f32 = c->prob.precision != MR_FP64;
   const void* kern;
   if (!f32)
     kern = c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1, double>
@@ -1582,7 +1582,7 @@ mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStr
           cudaSuccess ||
       cudaMemcpyAsync(S.ctl, hctl.data(), sizeof(RockCtl) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return MR_ECUDA;
-  const bool f32 = prec == MR_MIXED;
+  const bool f32 = prec != MR_FP64;
   const void* kern = m == 3 ? (f32 ? joint_kernel<3, float>() : joint_kernel<3, double>())
                             : (f32 ? joint_kernel<1, float>() : joint_kernel<1, double>());
   const int L = n * (m == 3 ? 3 : 1);

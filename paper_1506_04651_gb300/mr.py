@@ -16,7 +16,7 @@ from . import build as _build
 MR_OK = 0
 MR_MODEL_BZ, MR_MODEL_NAGUMO, MR_MODEL_NETWORK, MR_MODEL_IONIC = 1, 2, 3, 4
 IONIC_SPECIES = 21
-MR_FP64, MR_MIXED = 0, 1
+MR_FP64, MR_MIXED, MR_MIXED_F32_DETAILS = 0, 1, 2
 MAX_SPECIES, MAX_LEVEL = 32, 16
 NOALLOC_MAX_CELLS = 2147483647  # MR_NOALLOC_MAX_CELLS of include/mr.h
 

@@ -70,3 +70,32 @@ def test_mixed_strang_steps_against_fp64_oracle(mr):
     k_g, v_g = ctx.leaves()
     err = rel_l1(finest(k_g, v_g, 2, J), finest(k_o, v_o, 2, J))
     assert err <= 1e-5, err
+
+
+def test_fp32_details_option_against_fp64_oracle(mr):
+    """The mixed form with FP32 MR details (MR_MIXED_F32_DETAILS): ten steps of
+    the 2D J = 8 crossing fronts stay within 1e-5 (relative L1 over the
+    finest grid) of the FP64 oracle, and its adapted grid differs from the
+    FP64 path's in few leaves (only details within FP32 rounding of their
+    threshold can be tagged differently)."""
+    md = O.make_model("bz")
+    J, eta, nsteps = 8, 1e-3, 10
+    u0 = I.bz_cross_2d(J, 2)
+    T = O.Tree(2, J, 3, jmin=2)
+    T.set_full(u0)
+    T.adapt(eta)
+    c32 = mr.Context(mr.problem(2, J, precision=mr.MR_MIXED_F32_DETAILS))
+    c64 = mr.Context(mr.problem(2, J, precision=mr.MR_FP64))
+    c32.build(u0, eta)
+    c64.build(u0, eta)
+    for _ in range(nsteps):
+        assert T.strang(md, I.BZ_D, 1e-3, eta) == 0
+        c32.strang(1e-3, eta)
+        c64.strang(1e-3, eta)
+    k_o, v_o = T.leaves()
+    k_g, v_g = c32.leaves()
+    k_f, _ = c64.leaves()
+    assert np.array_equal(k_f, k_o)
+    err = rel_l1(finest(k_g, v_g, 2, J), finest(k_o, v_o, 2, J))
+    assert err <= 1e-5, err
+    assert len(np.setxor1d(k_g, k_o)) <= 0.01 * len(k_o)

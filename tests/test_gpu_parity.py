@@ -247,18 +247,32 @@ def test_nagumo_front_trajectory_matches_oracle(mr, d, J, eta):
     """NAGUMO (Sec. 1 item I: k = 10, diffusion 0.1, dt = 1e-2) from the
     travelling-front profile of a sphere / circle of radius 0.3, the bench's
     adaptation-heavy workload at a smaller finest level: the grids equal the
-    oracle's after each of five steps and the values agree to 1e-9."""
+    oracle's after each of five steps and the values agree to 1e-9, or to
+    the oracle's own rounding sensitivity where that is larger.
+
+    With diffusion 0.1 at J = 9 a ROCK4 step takes up to ~84 stages, and the
+    long recurrence amplifies rounding: a second oracle run, from the initial
+    state perturbed by 1e-16 relative, moves by ~1e-7 with the same step
+    decisions.  Two correct implementations that round differently can
+    differ by as much, so the bound is 20 times that spread (measured in
+    lockstep), and never below 1e-9."""
     md = O.make_model("nagumo", params=(I.NAGUMO_K,))
     u0 = I.nagumo_front(d, J)
-    T = O.Tree(d, J, 1, jmin=2)
+    up = u0 * (1.0 + 1e-16 * np.random.default_rng(3).standard_normal(u0.shape))
+    T, Tp = O.Tree(d, J, 1, jmin=2), O.Tree(d, J, 1, jmin=2)
     T.set_full(u0)
-    assert T.adapt(eta) == 0
+    Tp.set_full(up)
+    assert T.adapt(eta) == 0 and Tp.adapt(eta) == 0
     ctx = gpu_ctx(mr, d, J, model="nagumo")
     ctx.build(u0, eta)
     for s in range(5):
         assert T.strang(md, [I.NAGUMO_D], 1e-2, eta) == 0
+        assert Tp.strang(md, [I.NAGUMO_D], 1e-2, eta) == 0
         ctx.strang(1e-2, eta)
         k_o, v_o = T.leaves()
+        k_p, v_p = Tp.leaves()
         k_g, v_g = ctx.leaves()
         assert np.array_equal(k_o, k_g), s
-        assert rel_linf(v_g, v_o) <= 1e-9 * (s + 1), s
+        assert np.array_equal(k_o, k_p), s
+        spread = rel_linf(v_p, v_o)
+        assert rel_linf(v_g, v_o) <= max(1e-9 * (s + 1), 20.0 * spread), (s, spread)
