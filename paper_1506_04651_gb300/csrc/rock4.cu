@@ -167,6 +167,7 @@ struct RockCtl {
 
 struct PersArgs {
   int m, D, nb;
+  int J;         // finest level (the uniform-grid form's leaves are all at J)
   int64_t N, capL;
   double dt, tol, rho;
   double Dc[kMaxM];
@@ -284,7 +285,28 @@ __device__ inline void combine(const Ops<VT>& o, int64_t r, VT d, VT ih2, VT bet
   }
 }
 
-template <int D, int M, typename VT>
+// The faces of the level-J cell with Morton code c on the uniform grid, in
+// the regular-leaf table's order (x-, x+, y-, y+, z-, z+): the neighbour's
+// code, or c itself at the domain boundary (no flux, as in the table).
+template <int D>
+__device__ inline void uniform_faces(uint32_t c, int J, int* v) {
+  int k[3];
+  unmorton<D>(c, k);
+  const int lim = 1 << J;
+#pragma unroll
+  for (int f = 0; f < 2 * D; f++) {
+    const int a = f >> 1, sg = (f & 1) ? 1 : -1;
+    int q[3] = {k[0], k[1], k[2]};
+    q[a] += sg;
+    v[f] = (q[a] >= 0 && q[a] < lim) ? (int)morton<D>(q) : (int)c;
+  }
+}
+
+// CM: the uniform level-J grid (a Cartesian mesh: every leaf at level J, no
+// merged rows).  The leaf index is then the Morton code, and the sweeps take
+// the 2d neighbours from the code instead of the regular-leaf table, saving
+// its 32 bytes per leaf and sweep.
+template <int D, int M, typename VT, bool CM = false>
 __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     k_rock_persistent(PersArgs P, const int4* __restrict__ reg, int64_t nreg, IrrRows R,
                       const int32_t* __restrict__ irr_leaf, int64_t nirr) {
@@ -318,7 +340,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
   const int64_t tid = (threadIdx.x & 31) + 32 * (blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5)),
                 nth = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  const double leafb = N * (8.0 * D + 1.0);
+  const double leafb = CM ? 0.0 : N * (8.0 * D + 1.0);  // table bytes per sweep (none on the uniform grid)
   // vector q of species i: FP64: the state U (pool 0), W0..W2 (pool 1..3),
   // W3 (error accumulator), W4, W5 (L y); FP32: twelve float vectors carved
   // from the six work buffers, pool 0..3 = vectors 0..3 (vector 0 holds a
@@ -414,8 +436,16 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     const Ops<VT>* o = s_ops;
     const int* act = s_act;
     for (int64_t q = tid; q < nreg; q += nth) {
-      const int4 e0 = reg[2 * q], e1 = reg[2 * q + 1];
-      const int v[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+      int v[8];
+      if constexpr (CM) {
+        v[0] = (int)q;
+        uniform_faces<D>((uint32_t)q, P.J, v + 1);
+        v[1 + 2 * D] = P.J;
+      } else {
+        const int4 e0 = reg[2 * q], e1 = reg[2 * q + 1];
+        v[0] = e0.x; v[1] = e0.y; v[2] = e0.z; v[3] = e0.w;
+        v[4] = e1.x; v[5] = e1.y; v[6] = e1.z; v[7] = e1.w;
+      }
       const int64_t r = v[0];
       const int lev = v[1 + 2 * D];
       VT ih2;
@@ -1411,8 +1441,21 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
   const int M = m == 1 ? 1 : (m == 3 ? 3 : 16);
   // FP64 stage vectors, or FP32 in the mixed form
   const bool f32 = c->prob.precision != MR_FP64;
+  // the uniform finest grid (Cartesian mesh) sweeps without the table
+  const bool cm = N == c->n_level[c->J] && c->stats.irregular_rows == 0 && (M == 1 || M == 3);
   const void* kern;
-  if (!f32)
+  if (cm) {
+    if (!f32)
+      kern = c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1, double, true>
+                                 : (const void*)k_rock_persistent<2, 3, double, true>)
+                       : (M == 1 ? (const void*)k_rock_persistent<3, 1, double, true>
+                                 : (const void*)k_rock_persistent<3, 3, double, true>);
+    else
+      kern = c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1, float, true>
+                                 : (const void*)k_rock_persistent<2, 3, float, true>)
+                       : (M == 1 ? (const void*)k_rock_persistent<3, 1, float, true>
+                                 : (const void*)k_rock_persistent<3, 3, float, true>);
+  } else if (!f32)
     kern = c->d == 2 ? (M == 1 ? (const void*)k_rock_persistent<2, 1, double>
                                : (M == 3 ? (const void*)k_rock_persistent<2, 3, double>
                                          : (const void*)k_rock_persistent<2, 16, double>))
@@ -1449,6 +1492,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
     MR_CUDA(c, cudaMemcpyAsync(dctl, &hctl, sizeof hctl, cudaMemcpyHostToDevice, c->stream));
     P.m = mw;
     P.D = c->d;
+    P.J = c->J;
     P.nb = nb;
     P.N = N;
     P.capL = c->cap_leaves;
