@@ -92,9 +92,12 @@ enum { MR_FP64 = 0, MR_MIXED = 1, MR_MIXED_F32_DETAILS = 2 };
  *             diffused in windows of 16; windows whose coefficients are
  *             all zero cost nothing)
  *   precision MR_FP64, or MR_MIXED: Radau5 factorises and solves its Newton
- *             systems in FP32 and the ROCK4 stages run on FP32 vectors
- *             (Radau5 residuals, both error norms, step control, the state
- *             between sub-steps, details and mass stay FP64), or
+ *             systems in FP32, and the ROCK4 stages and finishing procedure
+ *             run on FP32 increments from the FP64 state (y_{n+1} - y_n and
+ *             the stage differences; L y_n is applied in FP64 once per
+ *             sub-step), so rounding is relative to the change a step makes
+ *             (Radau5 residuals, both error norms, step control, the state,
+ *             details and mass stay FP64), or
  *             MR_MIXED_F32_DETAILS: MR_MIXED with the MR details (Eq.
  *             detail) also predicted and differenced in FP32 from the FP64
  *             node values (thresholds and the normalisation stay FP64); the

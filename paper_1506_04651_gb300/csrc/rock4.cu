@@ -183,7 +183,7 @@ __device__ inline double ell_dev(int s) { return 0.336 * (double)s * s - 2.7; }
 // choose the next step of every species (one thread per block, on the
 // block's copy of the control)
 __device__ void rock_prepare(int m, double dt, const double* Dc, double rho_L, RockCtl& C, int64_t N,
-                             double leafb) {
+                             double leafb, bool inc = false) {
   int nmax = 0, any = 0;
   double bytes = 0.0;
   for (int i = 0; i < m; i++) {
@@ -217,9 +217,15 @@ __device__ void rock_prepare(int m, double dt, const double* Dc, double rho_L, R
     C.stages += s;
     C.smax = max(C.smax, s);
     C.matvecs += s + 1;
-    // vector bytes per leaf: stage 1 24, stages 2..n 24, Horner 16+24+32+40,
-    // embedded estimate 24 + 8 (keeps L y_{n+1})
-    bytes += N * (24.0 * (s - 4) + 112.0 + 32.0);
+    // vector bytes per leaf, each vector read or written once.  FP64: stage
+    // 1 24, stages 2..n 24, Horner 16+24+32+40, embedded estimate 24 + 8
+    // (keeps L y_{n+1}).  Mixed form (FP32 increments, FP64 state): stage 1
+    // 8 plus the FP64 state update 20, stage 2 12, stages 3..n 16, Horner
+    // 12+16+20+24, embedded estimate 24 (with the FP64 state for its scale)
+    if (inc)
+      bytes += N * (28.0 + (s >= 6 ? 12.0 + 16.0 * (s - 6) : 0.0) + 72.0 + 24.0);
+    else
+      bytes += N * (24.0 * (s - 4) + 112.0 + 32.0);
     any = 1;
   }
   C.nmax = nmax;
@@ -233,13 +239,32 @@ enum { K_STAGE = 0, K_H3, K_H2, K_H1, K_H0, K_FSAL, K_STAGE1 };
 constexpr int kPhaseFinish = 1000;  // phases 2..n: stages; kPhaseFinish + K_*: the other sweeps
 
 // VT: arithmetic of the stage vectors (double, or float in the mixed form);
-// the error norm is accumulated in double either way
+// the error norm is accumulated in double either way.
+//
+// The mixed form integrates increments: with y_n the FP64 state at the start
+// of a ROCK4 step and g = L y_n, every FP32 vector holds a difference from
+// y_n (or from its image under the Horner partial sums), so rounding is
+// relative to the change a step makes, not to the state.  Since every
+// stability polynomial is 1 at z = 0 (mu_j + nu_j = 1, w(0) = 1, and the
+// embedded estimate vanishes at z = 0), the recurrence and the finishing
+// procedure keep their form, with the term z y_n = h D g added:
+//   delta_1 = kap_1 h D g,
+//   delta_j = mu_j delta_{j-1} + nu_j delta_{j-2} + kap_j h D (g + L delta_{j-1}),
+//   eta_3 = w_3 delta + w_4 h D (g + L delta),
+//   eta_k = w_k delta + w_{k+1} h D g + h D L eta_{k+1}   (k = 2, 1),
+//   Delta = delta + w_1 h D g + h D L eta_1,   y_{n+1} = y_n + Delta (in FP64),
+//   E = e_0 delta + e_1 eta_1 + e_2 eta_2 + Delta + e_3 h D (g + L Delta),
+// and L y_{n+1} = g + L Delta is kept for the next step.  g itself is L y_n
+// applied in FP64 once per sub-step.
 template <typename VT>
 struct Ops {
   const VT *x, *a, *b, *yn;
   VT *out, *acc, *lx;
   VT ca, cb, cl, e0, e1, e2;
   int kind;
+  const VT* g;      // mixed form: L y_n (null in FP64)
+  VT cg;            // mixed form: weight of g
+  const double* u;  // mixed form: the FP64 state y_n (the error scale)
 };
 
 // d: the unscaled stencil sum (sum of the neighbours minus 2D times the
@@ -249,6 +274,41 @@ struct Ops {
 // the scaling multiply.
 template <typename VT>
 __device__ inline void combine(const Ops<VT>& o, int64_t r, VT d, VT ih2, VT beta, double tol, double& err) {
+  if constexpr (!std::is_same<VT, double>::value) {  // the mixed form's increments
+    switch (o.kind) {
+      case K_STAGE:
+        o.out[r] = o.ca * o.a[r] + (o.b ? o.cb * o.b[r] : (VT)0) + o.cl * o.g[r] + beta * d;
+        break;
+      case K_H3:
+      case K_H2:
+        o.out[r] = o.ca * o.a[r] + o.cg * o.g[r] + beta * d;
+        break;
+      case K_H1: {
+        const VT v = o.ca * o.a[r] + o.cg * o.g[r] + beta * d;
+        o.out[r] = v;
+        o.acc[r] = o.e0 * o.a[r] + o.e1 * v + o.e2 * o.x[r];
+        break;
+      }
+      case K_H0: {
+        const VT v = o.a[r] + o.cg * o.g[r] + beta * d;  // Delta
+        o.out[r] = v;
+        o.acc[r] += v;
+        break;
+      }
+      case K_FSAL: {  // L y_{n+1} = g + L Delta is kept; scale from y_n and y_n + Delta
+        const VT ly1 = o.g[r] + d * ih2;
+        o.lx[r] = ly1;
+        const double ee = (double)(o.acc[r] + o.cl * ly1);
+        const double yv = o.u[r];
+        const double sc = tol + tol * fmax(fabs(yv), fabs(yv + (double)o.x[r]));
+        err += (ee / sc) * (ee / sc);
+        break;
+      }
+      default:
+        break;  // K_STAGE1: the first stage reads the FP64 state (the g sweep)
+    }
+    return;
+  }
   switch (o.kind) {
     case K_STAGE:
       o.out[r] = o.ca * o.a[r] + o.cb * o.b[r] + beta * d;
@@ -318,6 +378,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
   __shared__ int s_py[kMaxM];   // pool index of the state
   __shared__ int s_pr[kMaxM][3];  // pool indices of the three recurrence buffers
   __shared__ int s_ly[kMaxM];   // which of W4 / W5 holds L y of the state
+  __shared__ int s_pend[kMaxM];  // mixed form: an accepted increment not yet added to the state
   __shared__ double s_err2[kMaxM];
   __shared__ Ops<VT> s_ops[M];
   __shared__ int s_act[M];
@@ -326,6 +387,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
   if (threadIdx.x == 0) {
     C = *P.ctl;
     for (int i = 0; i < M; i++) {
+      s_pend[i] = 0;
       s_py[i] = 0;
       s_pr[i][0] = 1;
       s_pr[i][1] = 2;
@@ -375,13 +437,21 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     o.acc = nullptr;
     o.lx = nullptr;
     o.yn = Y(i);
+    o.g = nullptr;
+    o.cg = (VT)0;
+    o.u = nullptr;
+    if constexpr (!kF64) {  // increments: g = L y_n, the FP64 state for the error scale
+      o.g = LY(i);
+      o.u = P.U + (int64_t)i * capL;
+    }
     if (phase < kPhaseFinish) {  // stage j >= 2
       const int j = phase;
       if (j > n) return false;
       o.kind = K_STAGE;
       o.x = Rb(i, (j - 2) % 3);
       o.a = o.x;
-      o.b = j == 2 ? Y(i) : Rb(i, (j - 3) % 3);
+      // P_0 = y_n: its increment delta_0 is zero
+      o.b = j == 2 ? (kF64 ? Y(i) : nullptr) : Rb(i, (j - 3) % 3);
       o.out = Rb(i, (j - 1) % 3);
       o.ca = (VT)tb[10 + (j - 1)];
       o.cb = (VT)tb[10 + n + (j - 1)];
@@ -397,13 +467,21 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
         o.x = Y(i); o.a = Y(i); o.out = Rb(i, 0); o.lx = LY(i);
         o.ca = (VT)tb[10]; o.cl = (VT)(tb[10 + 2 * n] * hd);
         break;
-      case K_H3: o.x = Rb(i, a); o.a = Rb(i, a); o.out = Rb(i, b); o.ca = (VT)w[3]; o.cl = (VT)(w[4] * hd); break;
-      case K_H2: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.ca = (VT)w[2]; o.cl = (VT)hd; break;
+      case K_H3:
+        o.x = Rb(i, a); o.a = Rb(i, a); o.out = Rb(i, b); o.ca = (VT)w[3]; o.cl = (VT)(w[4] * hd);
+        o.cg = (VT)(w[4] * hd);
+        break;
+      case K_H2:
+        o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.ca = (VT)w[2]; o.cl = (VT)hd; o.cg = (VT)(w[3] * hd);
+        break;
       case K_H1:
         o.x = Rb(i, cc); o.a = Rb(i, a); o.out = Rb(i, b); o.acc = Wp(3, i); o.ca = (VT)w[1]; o.cl = (VT)hd;
-        o.e0 = (VT)e[0]; o.e1 = (VT)e[1]; o.e2 = (VT)e[2];
+        o.e0 = (VT)e[0]; o.e1 = (VT)e[1]; o.e2 = (VT)e[2]; o.cg = (VT)(w[2] * hd);
         break;
-      case K_H0: o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.acc = Wp(3, i); o.ca = (VT)1; o.cl = (VT)hd; break;
+      case K_H0:
+        o.x = Rb(i, b); o.a = Rb(i, a); o.out = Rb(i, cc); o.acc = Wp(3, i); o.ca = (VT)1; o.cl = (VT)hd;
+        o.cg = (VT)(w[1] * hd);
+        break;
       default:
         o.x = Rb(i, cc); o.a = nullptr; o.out = nullptr; o.acc = Wp(3, i); o.lx = LC(i); o.cl = (VT)(e[3] * hd);
     }
@@ -511,18 +589,74 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
       }
     }
   };
-  __syncthreads();
-  if (threadIdx.x == 0) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, leafb);
-  __syncthreads();
-  if constexpr (!kF64) {
-    // the mixed form integrates a float copy of the state
-    for (int i = 0; i < P.m; i++) {
-      const double* u = P.U + (int64_t)i * capL;
-      VT* y = pool(i, 0);
-      for (int64_t r = tid; r < N; r += nth) y[r] = (VT)u[r];
+  // mixed form, first stage of a sub-step: g = L y_n applied to the FP64
+  // state in FP64 (kept as the float L y) and delta_1 = kap_1 h D g
+  auto gsweep = [&]() {
+    const Ops<VT>* o = s_ops;
+    const int* act = s_act;
+    for (int64_t q = tid; q < nreg; q += nth) {
+      int v[8];
+      if constexpr (CM) {
+        v[0] = (int)q;
+        uniform_faces<D>((uint32_t)q, P.J, v + 1);
+        v[1 + 2 * D] = P.J;
+      } else {
+        const int4 e0 = reg[2 * q], e1 = reg[2 * q + 1];
+        v[0] = e0.x; v[1] = e0.y; v[2] = e0.z; v[3] = e0.w;
+        v[4] = e1.x; v[5] = e1.y; v[6] = e1.z; v[7] = e1.w;
+      }
+      const int64_t r = v[0];
+      const double ih2 = c_ih2[v[1 + 2 * D]];
+#pragma unroll
+      for (int i = 0; i < M; i++) {
+        if (!act[i]) continue;
+        const double* u = P.U + (int64_t)i * capL;
+        double sx = u[v[1]];
+#pragma unroll
+        for (int f = 1; f < 2 * D; f++) sx += u[v[1 + f]];
+        const double gv = (sx - 2.0 * D * u[r]) * ih2;
+        o[i].lx[r] = (VT)gv;
+        o[i].out[r] = (VT)((double)o[i].cl * gv);
+      }
     }
-    grid.sync();
-  }
+    const int64_t grp = (D == 2 ? nth - 1 - tid : tid) / G, ngrp = nth / G;
+    const int64_t rounds = (nirr + ngrp - 1) / ngrp;
+    for (int64_t k = 0; k < rounds; k++) {
+      const int64_t row = grp + k * ngrp;
+      const bool have = row < nirr;
+      double v[M];
+#pragma unroll
+      for (int i = 0; i < M; i++) v[i] = 0.0;
+      int32_t r = 0;
+      if (have) {
+        r = irr_leaf[row];
+        const int cnt = R.cnt[row];
+        const int32_t* col = R.col + row * (int64_t)R.slot;
+        const double* wr = R.w + row * (int64_t)R.slot;
+        for (int e = sub; e < cnt; e += G) {
+          const int32_t cidx = col[e];
+          const double we = wr[e];
+#pragma unroll
+          for (int i = 0; i < M; i++)
+            if (act[i]) v[i] += we * P.U[(int64_t)i * capL + cidx];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < M; i++)
+        for (int sft = G / 2; sft > 0; sft >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], sft);
+      if (have && sub == 0) {
+#pragma unroll
+        for (int i = 0; i < M; i++)
+          if (act[i]) {
+            o[i].lx[r] = (VT)v[i];
+            o[i].out[r] = (VT)((double)o[i].cl * v[i]);
+          }
+      }
+    }
+  };
+  __syncthreads();
+  if (threadIdx.x == 0) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, leafb, !kF64);
+  __syncthreads();
   bool first = true;
   for (int round = 0; round < 20000; round++) {
     if (C.finished) break;
@@ -535,7 +669,10 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     // then an axpy on the kept L y)
     if (first) {
       build_ops(kPhaseFinish + K_STAGE1);
-      sweep(err, err_row);
+      if constexpr (kF64)
+        sweep(err, err_row);
+      else
+        gsweep();
     } else {
       for (int i = 0; i < M; i++) {
         if (C.done[i]) continue;
@@ -543,7 +680,21 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
         const VT ca = (VT)tb[10], cl = (VT)(tb[10 + 2 * C.n[i]] * C.h[i] * P.Dc[i]);
         const VT *y = Y(i), *ly = LY(i);
         VT* out = Rb(i, 0);
-        for (int64_t r = tid; r < N; r += nth) out[r] = ca * y[r] + cl * ly[r];
+        if constexpr (kF64) {
+          for (int64_t r = tid; r < N; r += nth) out[r] = ca * y[r] + cl * ly[r];
+        } else if (s_pend[i]) {
+          // the last accepted increment joins the FP64 state (it may share
+          // the buffer delta_1 goes to: read before the write)
+          double* u = P.U + (int64_t)i * capL;
+          const VT* dl = Rb(i, C.c_prev[i]);
+          for (int64_t r = tid; r < N; r += nth) {
+            const VT dv = dl[r];
+            u[r] += (double)dv;
+            out[r] = cl * ly[r];
+          }
+        } else {
+          for (int64_t r = tid; r < N; r += nth) out[r] = cl * ly[r];
+        }
       }
     }
     first = false;
@@ -594,6 +745,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
       for (int i = 0; i < M; i++) {
         C.acc_prev[i] = 0;
         if (C.done[i]) continue;
+        s_pend[i] = 0;  // consumed by this round's first stage
         const double err2 = sqrt(s_err2[i] / (double)N);
         C.err[i] = err2;
         if (!isfinite(err2)) {
@@ -603,11 +755,17 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
         }
         const double fac = err2 == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.8 * pow(err2, -0.25)));
         if (err2 <= 1.0) {
-          // the candidate y_{n+1} (recurrence buffer (a+2) % 3) becomes the state
+          // the candidate (recurrence buffer (a+2) % 3) becomes the state:
+          // FP64 by a buffer swap; the mixed form's increment Delta is added
+          // to the FP64 state by the next first stage (or at the end)
           const int cp = (C.a[i] + 2) % 3;
-          const int t = s_py[i];
-          s_py[i] = s_pr[i][cp];
-          s_pr[i][cp] = t;
+          if constexpr (kF64) {
+            const int t = s_py[i];
+            s_py[i] = s_pr[i][cp];
+            s_pr[i][cp] = t;
+          } else {
+            s_pend[i] = 1;
+          }
           s_ly[i] ^= 1;
           C.acc_prev[i] = 1;
           C.c_prev[i] = cp;
@@ -624,13 +782,19 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     __syncthreads();
   }
   if (threadIdx.x == 0 && !C.finished) C.status = MR_EROCK_STEP;
-  // the final state back into the state array where a swap moved it (FP64),
-  // or converted back (FP32)
+  // the final state into the state array where a swap moved it (FP64), or
+  // the last accepted increment added to it (mixed form)
   for (int i = 0; i < P.m; i++) {
-    if (kF64 && s_py[i] == 0) continue;
-    const VT* y = Y(i);
     double* u = P.U + (int64_t)i * capL;
-    for (int64_t r = tid; r < N; r += nth) u[r] = (double)y[r];
+    if constexpr (kF64) {
+      if (s_py[i] == 0) continue;
+      const VT* y = Y(i);
+      for (int64_t r = tid; r < N; r += nth) u[r] = (double)y[r];
+    } else {
+      if (!s_pend[i]) continue;
+      const VT* dl = Rb(i, C.c_prev[i]);
+      for (int64_t r = tid; r < N; r += nth) u[r] += (double)dl[r];
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.ctl = C;
 }
@@ -680,7 +844,9 @@ struct JArgs {
 struct PairCtl {
   double h;
   int s, n, a, on;  // on: the pair steps in this round
-  int py, pr[3], ly;
+  int py, pr[3], ly;  // pool indices; in the mixed form py is instead 1 while an
+                      // accepted increment waits to join the FP64 state
+  int cp;             // recurrence buffer of the last accepted candidate
 };
 
 // last k in [0, cnt) with off[k] <= q
@@ -771,6 +937,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
           p.pr[1] = __ldcg(pt + 2);
           p.pr[2] = __ldcg(pt + 3);
           p.ly = __ldcg(pt + 4);
+          p.cp = __ldcg(&C.c_prev[sp]);
         }
       }
       s_pc[l] = p;
@@ -786,19 +953,26 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
     const double* tb = A.tab.data + A.tab.off[p.s];
     const double hd = p.h * I.Dc[sp];
     const int nn = p.n;
-    VT* Y = pool(I, sp, p.py);
+    VT* Y = pool(I, sp, kF64 ? p.py : 0);
     auto Rb = [&](int q) { return pool(I, sp, p.pr[q]); };
     o.b = nullptr;
     o.acc = nullptr;
     o.lx = nullptr;
     o.yn = Y;
+    o.g = nullptr;
+    o.cg = (VT)0;
+    o.u = nullptr;
+    if constexpr (!kF64) {  // increments: g = L y_n, the FP64 state for the error scale
+      o.g = Wp(I, sp, 4 + p.ly);
+      o.u = I.U + (int64_t)sp * I.capL;
+    }
     if (phase < kPhaseFinish) {  // stage j >= 2
       const int j = phase;
       if (j > nn) return false;
       o.kind = K_STAGE;
       o.x = Rb((j - 2) % 3);
       o.a = o.x;
-      o.b = j == 2 ? Y : Rb((j - 3) % 3);
+      o.b = j == 2 ? (kF64 ? Y : nullptr) : Rb((j - 3) % 3);
       o.out = Rb((j - 1) % 3);
       o.ca = (VT)tb[10 + (j - 1)];
       o.cb = (VT)tb[10 + nn + (j - 1)];
@@ -813,14 +987,21 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
       case K_STAGE1:
         o.x = Y; o.a = Y; o.out = Rb(0); o.lx = Wp(I, sp, 4 + p.ly);
         o.ca = (VT)tb[10]; o.cl = (VT)(tb[10 + 2 * nn] * hd);
+        // mixed form: the accepted increment still to be added to the state
+        if (!kF64 && p.py) o.b = Rb(p.cp);
         break;
-      case K_H3: o.x = Rb(a); o.a = Rb(a); o.out = Rb(b); o.ca = (VT)w[3]; o.cl = (VT)(w[4] * hd); break;
-      case K_H2: o.x = Rb(b); o.a = Rb(a); o.out = Rb(cc); o.ca = (VT)w[2]; o.cl = (VT)hd; break;
+      case K_H3:
+        o.x = Rb(a); o.a = Rb(a); o.out = Rb(b); o.ca = (VT)w[3]; o.cl = (VT)(w[4] * hd); o.cg = (VT)(w[4] * hd);
+        break;
+      case K_H2: o.x = Rb(b); o.a = Rb(a); o.out = Rb(cc); o.ca = (VT)w[2]; o.cl = (VT)hd; o.cg = (VT)(w[3] * hd); break;
       case K_H1:
         o.x = Rb(cc); o.a = Rb(a); o.out = Rb(b); o.acc = Wp(I, sp, 3); o.ca = (VT)w[1]; o.cl = (VT)hd;
-        o.e0 = (VT)e[0]; o.e1 = (VT)e[1]; o.e2 = (VT)e[2];
+        o.e0 = (VT)e[0]; o.e1 = (VT)e[1]; o.e2 = (VT)e[2]; o.cg = (VT)(w[2] * hd);
         break;
-      case K_H0: o.x = Rb(b); o.a = Rb(a); o.out = Rb(cc); o.acc = Wp(I, sp, 3); o.ca = (VT)1; o.cl = (VT)hd; break;
+      case K_H0:
+        o.x = Rb(b); o.a = Rb(a); o.out = Rb(cc); o.acc = Wp(I, sp, 3); o.ca = (VT)1; o.cl = (VT)hd;
+        o.cg = (VT)(w[1] * hd);
+        break;
       default:
         o.x = Rb(cc); o.a = nullptr; o.out = nullptr; o.acc = Wp(I, sp, 3); o.lx = Wp(I, sp, 5 - p.ly);
         o.cl = (VT)(e[3] * hd);
@@ -972,6 +1153,78 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
       }
     }
   };
+  // mixed form, first stage of the sub-step: g = L y_n of every active pair
+  // applied to the FP64 state in FP64 (kept as the float L y) and
+  // delta_1 = kap_1 h D g, over the active instances as in sweep()
+  auto gsweep = [&]() {
+    const int na = s_nact;
+    const int64_t nreg = creg[na], nirr = cirr[na];
+    int k = -1;
+    for (int64_t q = tid; q < nreg; q += nth) {
+      seek(creg, na, q, k);
+      const int i = s_cmap[k];
+      const JInst& I = A.inst[i];
+      const int64_t ql = q - creg[k];
+      const int4 e0 = I.reg[2 * ql], e1 = I.reg[2 * ql + 1];
+      const int v[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+      const int64_t r = v[0];
+      const double ih2 = c_ih2[v[1 + 2 * D]];
+#pragma unroll
+      for (int sp = 0; sp < M; sp++) {
+        const int l = i * M + sp;
+        if (!s_act[l]) continue;
+        const Ops<VT>& o = s_ops[l];
+        const double* u = I.U + (int64_t)sp * I.capL;
+        double sx = u[v[1]];
+#pragma unroll
+        for (int f = 1; f < 2 * D; f++) sx += u[v[1 + f]];
+        const double gv = (sx - 2.0 * D * u[r]) * ih2;
+        o.lx[r] = (VT)gv;
+        o.out[r] = (VT)((double)o.cl * gv);
+      }
+    }
+    const int64_t grp = (nth - 1 - tid) / G, ngrp = nth / G;
+    const int64_t rounds = (nirr + ngrp - 1) / ngrp;
+    k = -1;
+    for (int64_t kk = 0; kk < rounds; kk++) {
+      const int64_t row = grp + kk * ngrp;
+      const bool have = row < nirr;
+      int i = 0;
+      double vs[M];
+#pragma unroll
+      for (int sp = 0; sp < M; sp++) vs[sp] = 0.0;
+      int32_t r = 0;
+      if (have) {
+        seek(cirr, na, row, k);
+        i = s_cmap[k];
+        const JInst& I = A.inst[i];
+        const int64_t rl = row - cirr[k];
+        r = I.irr_leaf[rl];
+        const int cnt = I.cnt[rl];
+        const int32_t* col = I.col + rl * (int64_t)I.slot;
+        const double* wr = I.w + rl * (int64_t)I.slot;
+        for (int e = sub; e < cnt; e += G) {
+          const int32_t cidx = col[e];
+          const double we = wr[e];
+#pragma unroll
+          for (int sp = 0; sp < M; sp++)
+            if (s_act[i * M + sp]) vs[sp] += we * I.U[(int64_t)sp * I.capL + cidx];
+        }
+      }
+#pragma unroll
+      for (int sp = 0; sp < M; sp++)
+        for (int sft = G / 2; sft > 0; sft >>= 1) vs[sp] += __shfl_xor_sync(0xffffffffu, vs[sp], sft);
+      if (have && sub == 0) {
+#pragma unroll
+        for (int sp = 0; sp < M; sp++)
+          if (s_act[i * M + sp]) {
+            const Ops<VT>& o = s_ops[i * M + sp];
+            o.lx[r] = (VT)vs[sp];
+            o.out[r] = (VT)((double)o.cl * vs[sp]);
+          }
+      }
+    }
+  };
   // accept / reject and the next step of instance i (one thread of block 0)
   auto control = [&](int i) {
     RockCtl& C = A.ctl[i];
@@ -989,13 +1242,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
         break;
       }
       const double fac = err == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.8 * pow(err, -0.25)));
+      int* pt = A.ptr + 5 * (i * kMaxM + sp);
+      if (!kF64) pt[0] = 0;  // the pending increment was added by this round's first stage
       if (err <= 1.0) {
-        // the candidate y_{n+1} (recurrence buffer (a+2) % 3) becomes the state
-        int* pt = A.ptr + 5 * (i * kMaxM + sp);
+        // the candidate (recurrence buffer (a+2) % 3) becomes the state: by a
+        // buffer swap (FP64), or its increment joins the FP64 state at the
+        // next first stage or at the end (mixed form)
         const int cp = (C.a[sp] + 2) % 3;
-        const int t = pt[0];
-        pt[0] = pt[1 + cp];
-        pt[1 + cp] = t;
+        if constexpr (kF64) {
+          const int t = pt[0];
+          pt[0] = pt[1 + cp];
+          pt[1 + cp] = t;
+        } else {
+          pt[0] = 1;
+        }
         pt[4] ^= 1;
         C.acc_prev[sp] = 1;
         C.c_prev[sp] = cp;
@@ -1007,7 +1267,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
       C.h[sp] *= fac;
     }
     C.rounds++;
-    if (!C.finished) rock_prepare(A.m, A.dt, I.Dc, I.rho, C, I.N, I.N * (8.0 * D + 1.0));
+    if (!C.finished) rock_prepare(A.m, A.dt, I.Dc, I.rho, C, I.N, I.N * (8.0 * D + 1.0), !kF64);
   };
   auto publish = [&]() {  // block 0: the flags every block reads after the next barrier
     if (blockIdx.x == 0) {
@@ -1029,7 +1289,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const JInst& I = A.inst[i];
-      rock_prepare(A.m, A.dt, I.Dc, I.rho, A.ctl[i], I.N, I.N * (8.0 * D + 1.0));
+      rock_prepare(A.m, A.dt, I.Dc, I.rho, A.ctl[i], I.N, I.N * (8.0 * D + 1.0), !kF64);
       for (int sp = 0; sp < kMaxM; sp++) {
         int* pt = A.ptr + 5 * (i * kMaxM + sp);
         pt[0] = 0;
@@ -1042,15 +1302,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
   }
   publish();
   const int64_t nleaf_all = leaf_off[n];
-  if constexpr (!kF64) {  // the mixed form integrates a float copy of the state
-    int k = -1;
-    for (int64_t q = tid; q < nleaf_all; q += nth) {
-      seek(leaf_off, n, q, k);
-      const JInst& I = A.inst[k];
-      const int64_t r = q - leaf_off[k];
-      for (int sp = 0; sp < A.m; sp++) pool(I, sp, 0)[r] = (VT)I.U[(int64_t)sp * I.capL + r];
-    }
-  }
   grid.sync();
   bool first = true;
   for (int round = 0; round < 20000; round++) {
@@ -1061,7 +1312,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
     // then an axpy on the kept L y)
     build_ops(kPhaseFinish + K_STAGE1);
     if (first) {
-      sweep();
+      if constexpr (kF64)
+        sweep();
+      else
+        gsweep();
     } else {
       const int na = s_nact;
       const int64_t nl = cleaf[na];
@@ -1075,7 +1329,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
           const int l = i * M + sp;
           if (!s_act[l]) continue;
           const Ops<VT>& o = s_ops[l];
-          o.out[r] = o.ca * o.a[r] + o.cl * o.lx[r];
+          if constexpr (kF64) {
+            o.out[r] = o.ca * o.a[r] + o.cl * o.lx[r];
+          } else {
+            if (o.b) {  // the accepted increment joins the FP64 state (read before delta_1 is written)
+              const VT dv = o.b[r];
+              A.inst[i].U[(int64_t)sp * A.inst[i].capL + r] += (double)dv;
+            }
+            o.out[r] = o.cl * o.lx[r];
+          }
         }
       }
     }
@@ -1121,17 +1383,23 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < n; i += blockDim.x)
       if (!A.ctl[i].finished) A.ctl[i].status = MR_EROCK_STEP;
-  // the final states back into the state arrays where a swap moved them
-  // (FP64), or converted back (FP32)
+  // the final states into the state arrays where a swap moved them (FP64),
+  // or the last accepted increments added to them (mixed form)
   int k = -1;
   for (int64_t q = tid; q < nleaf_all; q += nth) {
     seek(leaf_off, n, q, k);
     const JInst& I = A.inst[k];
     const int64_t r = q - leaf_off[k];
     for (int sp = 0; sp < A.m; sp++) {
-      const int py = __ldcg(A.ptr + 5 * (k * kMaxM + sp));
-      if (kF64 && py == 0) continue;
-      I.U[(int64_t)sp * I.capL + r] = (double)pool(I, sp, py)[r];
+      const int* pt = A.ptr + 5 * (k * kMaxM + sp);
+      const int py = __ldcg(pt);
+      if (py == 0) continue;
+      if constexpr (kF64) {
+        I.U[(int64_t)sp * I.capL + r] = (double)pool(I, sp, py)[r];
+      } else {
+        const int cp = __ldcg(&A.ctl[k].c_prev[sp]);
+        I.U[(int64_t)sp * I.capL + r] += (double)pool(I, sp, __ldcg(pt + 1 + cp))[r];
+      }
     }
   }
 }
