@@ -431,13 +431,11 @@ def run_gpu(args, w):
                 "peak_source": "measured FP64 FMA rate of this GPU (library probe, 2 flop/FMA)",
                 "launches": rad_n, "ms_per_launch": rad_ms / max(rad_n, 1)}
     else:
-        ach = rock_b / (rock_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_rock (ROCK4 sweep, FP64)", "achieved": ach,
-                "peak": hbm or 6800.0, "unit": "GB/s", "frac": ach / (hbm or 6800.0),
-                "traffic": profiled_traffic("rock4.cu", "k_rock_persistent_bz2d_J10.md")
-                if args.workload == DEFAULT else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s",
-                "launches": rock_n, "ms_per_launch": rock_ms / max(rock_n, 1)}
+        roof = rock_roofline(rock_b, st1["rock_alg_flops"] - st0["rock_alg_flops"], rock_ms, hbm, fp64_tf,
+                             mixed_form=False)
+        roof.update({"traffic": profiled_traffic("rock4.cu", "k_rock_persistent_bz2d_J10.md")
+                     if args.workload == DEFAULT else None, "launches": rock_n,
+                     "ms_per_launch": rock_ms / max(rock_n, 1)})
     # adaptation: algorithmic bytes per step = for the tree before and after
     # (about the same size), every node's m values (8 B each), code (4 B) and
     # level (1 B) read or written once, plus its tag byte
@@ -452,12 +450,8 @@ def run_gpu(args, w):
                   "note": "algorithmic bytes (values, code, level and tag of every node of the old and new tree, "
                           "once) over the phase's event time per step; the phase is launch- and latency-bound "
                           "(tens of small kernels, a few host synchronisations to size the new tree)"}
-    rock_ach = rock_b / (rock_ms * 1e-3) / 1e9 if rock_ms else 0.0
-    roof_rock = {"bound": "hbm", "kernel": "k_rock_persistent (ROCK4 sweeps, whole diffusion sub-step)",
-                 "achieved": rock_ach, "peak": hbm or 6800.0, "unit": "GB/s", "frac": rock_ach / (hbm or 6800.0),
-                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s",
-                 "note": "algorithmic bytes of the sweeps (tables once per sweep, vectors read and written once) "
-                         "over the launch time; a roofline only where the leaf vectors exceed L2"}
+    roof_rock = rock_roofline(rock_b, st1["rock_alg_flops"] - st0["rock_alg_flops"], rock_ms, hbm, fp64_tf,
+                              mixed_form=False)
     rad_cnt = [b - a for a, b in zip(st0["radau_counters"], st1["radau_counters"])]
     work = radau_work(w.get("model", "bz"), ctx.m)
     kernels = {"radau": {"ms": rad_ms, "launches": rad_n, "tflops": rad_fl / max(rad_ms, 1e-9) / 1e9,
@@ -517,6 +511,10 @@ def run_gpu(args, w):
     # the same number of steps from the same initial grid; its final state is
     # compared with the FP64 path's after the same steps (relative L1 on the
     # finest grid)
+    # the leaf operator in its compact form against the same operator as a
+    # CSR matrix, on the tree the timed steps ended with (App. C, Table 5)
+    forms = ctx.operator_forms(reps=50)
+    forms["ratio_compact_over_csr"] = forms["ms_compact"] / forms["ms_csr"]
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(args, w, mr, torch, dev, stream, u0)
@@ -566,6 +564,7 @@ def run_gpu(args, w):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roof, "roofline_rock4": roof_rock, "roofline_adapt": roof_adapt, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "mixed": mixed, "hbm_point": hbm_point,
+            "operator_forms": forms,
             "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
     if conservation:
         line["conservation"] = conservation
@@ -607,6 +606,28 @@ def rel_l1_finest(ka, va, kb, vb, d, J):
     return max(float(np.sum(np.abs(A[i] - B[i])) / max(np.sum(np.abs(B[i])), 1e-300)) for i in range(len(B)))
 
 
+def rock_roofline(nbytes, flops, ms, hbm, fp64_tf, mixed_form):
+    """The ROCK4 sweeps against their binding limit: HBM bandwidth, or for
+    the FP64 form the FP64 pipe at the sweeps' arithmetic intensity
+    (flops per algorithmic byte), whichever is lower."""
+    peak_hbm = hbm or 6800.0
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms else 0.0
+    fpb = flops / nbytes if nbytes else 0.0
+    fp64_bound = fp64_tf * 1e3 / fpb if fpb and not mixed_form else None
+    binding = min(peak_hbm, fp64_bound) if fp64_bound else peak_hbm
+    return {"bound": "hbm" if binding == peak_hbm else "alu",
+            "kernel": "k_rock_persistent (ROCK4 sweeps, whole diffusion sub-step)",
+            "achieved": gbs, "peak": binding, "unit": "GB/s", "frac": gbs / binding,
+            "hbm_peak": peak_hbm, "frac_of_hbm": gbs / peak_hbm,
+            "peak_source": ("min(HBM, FP64 FMA rate x bytes per flop)" if not mixed_form else "HBM") +
+                           (" -- HBM from MEASURED_PEAKS.json (of measured)" if hbm else " -- HBM fallback 6.8 TB/s"),
+            "flops": flops, "flops_per_byte": fpb,
+            "tflops": flops / (ms * 1e-3) / 1e12 if ms else 0.0,
+            "frac_of_fp64_peak": (flops / (ms * 1e-3) / 1e12) / fp64_tf if ms and not mixed_form else None,
+            "note": "algorithmic bytes of the sweeps (tables and merged rows once per sweep, vectors read and "
+                    "written once) and their arithmetic, over the launch time"}
+
+
 def run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf, steps=3, warmup=2):
     """The HBM-resident point of the 3D BZ workload (J = 9, 512^3 finest,
     leaf vectors larger than L2) as a bounded extra of the default line: a
@@ -639,6 +660,7 @@ def run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf, steps=3, warmup=2):
         ph["react_both_halves"] += sk["ms_react"]
         ph["diffuse"] += sk["ms_diffuse"]
     st1 = ctx.stats()
+    forms = ctx.operator_forms(reps=20)
     ctx.close()
     peak = hbm or 6800.0
     rock_ms = st1["rock_kernel_ms"] - st0["rock_kernel_ms"]
@@ -652,15 +674,17 @@ def run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf, steps=3, warmup=2):
             "leaves_last_step": st1["leaves"], "irregular_rows": st1["irregular_rows"],
             "irregular_nnz": st1["irregular_nnz"],
             "phase_ms_per_step": {k: v / steps for k, v in ph.items()},
-            "roofline_rock4": {"bound": "hbm", "achieved": rock_b / (rock_ms * 1e-3) / 1e9, "peak": peak,
-                               "unit": "GB/s", "frac": rock_b / (rock_ms * 1e-3) / 1e9 / peak,
-                               "ms_per_launch": rock_ms / max(1, st1["rock_kernel_launches"] -
-                                                              st0["rock_kernel_launches"])},
+            "roofline_rock4": dict(rock_roofline(rock_b, st1["rock_alg_flops"] - st0["rock_alg_flops"], rock_ms,
+                                                 hbm, fp64_tf, mixed_form=False),
+                                   ms_per_launch=rock_ms / max(1, st1["rock_kernel_launches"] -
+                                                               st0["rock_kernel_launches"])),
             "roofline_adapt": {"bound": "hbm", "achieved": adapt_b / (adapt_ms * 1e-3) / 1e9, "peak": peak,
                                "unit": "GB/s", "frac": adapt_b / (adapt_ms * 1e-3) / 1e9 / peak},
             "roofline_radau": {"bound": "alu", "achieved": rad_fl / (rad_ms * 1e-3) / 1e12, "peak": fp64_tf,
                                "unit": "TFLOP/s", "frac": rad_fl / (rad_ms * 1e-3) / 1e12 / fp64_tf},
             "l2": "flushed before every timed step (256 MB write); state and work vectors exceed L2",
+            "operator_forms": dict(forms, ratio_compact_over_csr=forms["ms_compact"] / forms["ms_csr"],
+                                   paper_ratio_3d="0.67 (BZ 3D J=10, 40 Haswell threads, App. C Table 5)"),
             "wall_s": time.perf_counter() - t0}
 
 

@@ -141,6 +141,14 @@ typedef struct {
   /* cumulative Radau5 counters since mr_create: f evaluations, Jacobians, step
    * attempts, accepted, rejected, Newton iterations, factorisations, cells */
   int64_t radau_counters[8];
+  /* cumulative arithmetic of the ROCK4 sweeps since mr_create: per operator
+   * application 2d + 1 per regular leaf and 2 per merged-row entry, plus the
+   * stage and finishing combinations (5 per stage, 3 + 3 + 8 + 4 for the
+   * finishing sweeps, 8 for the estimate, 3 for the first stage); FP64
+   * operations in the FP64 form, FP32 in the mixed form.  rock_alg_bytes
+   * counts the merged rows too (12 bytes per entry in FP64, 8 in the mixed
+   * form, 8 per row). */
+  double rock_alg_flops;
 } mr_stats;
 
 /* Create a context for `prob` on `cuda_stream` (a cudaStream_t or NULL).
@@ -301,6 +309,22 @@ mr_status mr_mass(mr_ctx *ctx, double *mass);
  * (may be NULL).  For checking the operator the library builds. */
 mr_status mr_apply_operator(mr_ctx *ctx, const double *u_in, double *out, int on_device,
                             double *rho);
+
+/* The two storage forms of the leaf operator L and their cost per
+ * application: the comparison of App. C (Table 5: the paper's compact
+ * operator against a CSR matrix of the same operator).  "Compact" is the form
+ * the ROCK4 sweeps use: a regular-leaf table (the leaf, its 2d same-level
+ * neighbours and its level; weights 1/h^2 implicit) and one merged
+ * (leaf, weight) row per leaf at a level jump.  "CSR" assembles every row
+ * into one compressed sparse row matrix.  Each form is applied `reps` times
+ * (1..10000) to one FP64 vector of the current tree after a warm-up; *ms_* get
+ * the mean device time of one application (CUDA events on the context
+ * stream), *csr_nnz the CSR matrix's entries and *max_rel_diff max |L_csr u -
+ * L_compact u| / max |L_compact u|.  The CSR matrix and the vectors are
+ * allocated for the call and freed before it returns.  MR_EINVAL for bad
+ * arguments; MR_ECUDA if an allocation or launch fails. */
+mr_status mr_operator_forms(mr_ctx *ctx, int reps, double *ms_compact, double *ms_csr, int64_t *csr_nnz,
+                            double *max_rel_diff);
 
 /* The library's ROCK4-type coefficients for s stages (5 <= s <= 152): the
  * recurrence P_{j+1} = mu[j+1] P_j + nu[j+1] P_{j-1} + kap[j+1] z P_j

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmrgb300.so")
-SOURCES = ["batch.cu", "ctx.cu", "mr.cu", "radau5.cu", "radau5_net.cu", "rock4.cu", "scan.cu"]
+SOURCES = ["batch.cu", "ctx.cu", "mr.cu", "opforms.cu", "radau5.cu", "radau5_net.cu", "rock4.cu", "scan.cu"]
 HEADERS = ["mr_internal.cuh", "radau_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -572,6 +572,13 @@ mr_status mr_apply_operator(mr_ctx* c, const double* u_in, double* out, int on_d
   return s;
 }
 
+mr_status mr_operator_forms(mr_ctx* c, int reps, double* ms_compact, double* ms_csr, int64_t* csr_nnz,
+                            double* max_rel_diff) {
+  if (check_ctx(c) || !ms_compact || !ms_csr || !csr_nnz || !max_rel_diff || reps < 1 || reps > 10000)
+    return MR_EINVAL;
+  return operator_forms(c, reps, ms_compact, ms_csr, csr_nnz, max_rel_diff);
+}
+
 mr_status mr_fp64_fma_rate(double* tflops, double* mhz) {
   if (!tflops) return MR_EINVAL;
   return fp64_probe(tflops, mhz);

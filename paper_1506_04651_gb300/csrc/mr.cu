@@ -22,6 +22,7 @@
 // down.  Nodes are then renumbered without sorting: an exclusive scan over
 // the refined flags of all levels gives each refined cell its rank g, and its
 // children are nodes 1 + 2^d g ... 2^d (g + 1) (level-major Morton order).
+#include <cooperative_groups.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -54,30 +55,38 @@ struct Level {
 };
 
 // ------------------------------------------------------------ projection
-__global__ void k_scatter_leaves(const double* __restrict__ U, const int32_t* __restrict__ leaf_node,
-                                 double* __restrict__ V, int64_t N, int m, int64_t capL,
-                                 int64_t capN) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    int32_t n = leaf_node[r];
-    for (int i = 0; i < m; i++) V[i * capN + n] = U[i * capL + r];
+// parent = mean of its 2^d children, summed in child order (Sec. 2.2)
+template <int D>
+__device__ inline void project_node(double* __restrict__ V, const int32_t* __restrict__ first_child, int64_t n,
+                                    int m, int64_t capN) {
+  int32_t fc = first_child[n];
+  if (fc < 0) return;
+  for (int i = 0; i < m; i++) {
+    const double* v = V + i * capN + fc;
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < (1 << D); t++) s = __dadd_rn(s, v[t]);
+    V[i * capN + n] = s / (double)(1 << D);
   }
 }
 
+// The whole projection in one cooperative launch: the leaf values into the
+// node array, then levels J-1 .. 0 bottom-up with a grid barrier between
+// levels (one launch instead of J + 1).
 template <int D>
-__global__ void k_project_level(double* __restrict__ V, const int32_t* __restrict__ first_child,
-                                int64_t lo, int64_t hi, int m, int64_t capN) {
-  for (int64_t n = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < hi;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    int32_t fc = first_child[n];
-    if (fc < 0) continue;
-    for (int i = 0; i < m; i++) {
-      const double* v = V + i * capN + fc;
-      double s = 0.0;
-#pragma unroll
-      for (int t = 0; t < (1 << D); t++) s = __dadd_rn(s, v[t]);
-      V[i * capN + n] = s / (double)(1 << D);
-    }
+__global__ void k_project_all(const double* __restrict__ U, const int32_t* __restrict__ leaf_node,
+                              double* __restrict__ V, const int32_t* __restrict__ first_child, Level L, int J,
+                              int64_t N, int m, int64_t capL, int64_t capN) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = tid; r < N; r += nth) {
+    const int32_t n = leaf_node[r];
+    for (int i = 0; i < m; i++) V[i * capN + n] = U[i * capL + r];
+  }
+  for (int j = J - 1; j >= 0; j--) {
+    grid.sync();
+    for (int64_t n = L.noff[j] + tid; n < L.noff[j + 1]; n += nth) project_node<D>(V, first_child, n, m, capN);
   }
 }
 
@@ -198,31 +207,25 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
 }
 
 // ------------------------------------------------------------ adaptation sweep
-__global__ void k_flags_init(const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
-                             const int32_t* __restrict__ first_child, const uint8_t* __restrict__ tag,
-                             Level L, int64_t nint, int J, uint8_t* __restrict__ state) {
-  // nodes of levels < J are the first nint nodes (level-major order)
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nint;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    int j = lvl[n];
-    uint8_t f = 0;
-    if (first_child[n] >= 0) f |= F_OLD_INT;
-    if (n > 0 && tag[n]) {
-      f |= F_TAG;
-      if (first_child[n] < 0) f |= F_LEAF_TAG;
-    }
-    (void)J;
-    state[L.doff[j] + code[n]] = f;
+// the flags of node n (of a level < J) in the dense level maps
+__device__ inline void flags_node(const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
+                                  const int32_t* __restrict__ first_child, const uint8_t* __restrict__ tag,
+                                  const Level& L, int64_t n, uint8_t* __restrict__ state) {
+  int j = lvl[n];
+  uint8_t f = 0;
+  if (first_child[n] >= 0) f |= F_OLD_INT;
+  if (n > 0 && tag[n]) {
+    f |= F_TAG;
+    if (first_child[n] < 0) f |= F_LEAF_TAG;
   }
+  state[L.doff[j] + code[n]] = f;
 }
 
 template <int D>
-__global__ void k_sweep_level(const uint8_t* __restrict__ state, uint8_t* __restrict__ forced,
-                              uint8_t* __restrict__ final_, Level L, int i, int jmin) {
-  const int64_t n = (int64_t)1 << (D * i);
+__device__ inline void sweep_cell(const uint8_t* __restrict__ state, uint8_t* __restrict__ forced,
+                                  uint8_t* __restrict__ final_, const Level& L, int i, int jmin, int64_t p) {
   const int64_t base = L.doff[i];
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
+  {
     uint8_t st = state[base + p];
     uint8_t fo = forced[base + p];
     bool cand = (st & (F_OLD_INT | F_LEAF_TAG)) || fo;
@@ -247,6 +250,25 @@ __global__ void k_sweep_level(const uint8_t* __restrict__ state, uint8_t* __rest
         if (in) forced[pb + morton<D>(q)] = 1;
       }
     }
+  }
+}
+
+// The flags and the whole downward sweep in one cooperative launch: the
+// flags of the old tree's nodes of levels < J, then levels J-1 .. 0 with a
+// grid barrier between levels (a level's cells force cells one level down).
+template <int D>
+__global__ void k_sweep_all(const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl,
+                            const int32_t* __restrict__ first_child, const uint8_t* __restrict__ tag, Level L,
+                            int64_t nint, int J, int jmin, uint8_t* __restrict__ state,
+                            uint8_t* __restrict__ forced, uint8_t* __restrict__ final_) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = tid; n < nint; n += nth) flags_node(code, lvl, first_child, tag, L, n, state);
+  for (int i = J - 1; i >= 0; i--) {
+    grid.sync();
+    const int64_t ncell = (int64_t)1 << (D * i);
+    for (int64_t p = tid; p < ncell; p += nth) sweep_cell<D>(state, forced, final_, L, i, jmin, p);
   }
 }
 
@@ -325,35 +347,47 @@ __global__ void k_leaf_lists(const int32_t* __restrict__ first_child, const int3
 // values of the new tree, level j: old nodes keep their value, new nodes are
 // predicted from the new tree's level j-1 (whose stencils exist: graded)
 template <int D>
-__global__ void k_new_values(const uint32_t* __restrict__ code, int64_t lo, int64_t hi, int j,
-                             const int32_t* __restrict__ dmap_old, const int32_t* __restrict__ dmap_new,
-                             Level L, const double* __restrict__ Vold, double* __restrict__ Vnew,
-                             int m, int64_t capN, DevCounters* dc) {
-  for (int64_t n = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < hi;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t c = code[n];
-    int32_t o = dmap_old[L.doff[j] + c];
-    if (o >= 0) {
-      for (int i = 0; i < m; i++) Vnew[i * capN + n] = Vold[i * capN + o];
-    } else {
-      int k[3];
-      unmorton<D>(c, k);
-      const int32_t* dm = dmap_new + L.doff[j - 1];
-      for (int i = 0; i < m; i++) {
-        double v = predict<D>(Vnew, dm, k, j - 1, capN, i);
-        if (isnan(v)) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
-        Vnew[i * capN + n] = v;
-      }
+__device__ inline void new_value_node(const uint32_t* __restrict__ code, int64_t n, int j,
+                                      const int32_t* __restrict__ dmap_old, const int32_t* __restrict__ dmap_new,
+                                      const Level& L, const double* __restrict__ Vold, double* __restrict__ Vnew,
+                                      int m, int64_t capN, DevCounters* dc) {
+  uint32_t c = code[n];
+  int32_t o = dmap_old[L.doff[j] + c];
+  if (o >= 0) {
+    for (int i = 0; i < m; i++) Vnew[i * capN + n] = Vold[i * capN + o];
+  } else {
+    int k[3];
+    unmorton<D>(c, k);
+    const int32_t* dm = dmap_new + L.doff[j - 1];
+    for (int i = 0; i < m; i++) {
+      double v = predict<D>(Vnew, dm, k, j - 1, capN, i);
+      if (isnan(v)) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
+      Vnew[i * capN + n] = v;
     }
   }
 }
 
-__global__ void k_gather_leaves(const double* __restrict__ V, const int32_t* __restrict__ leaf_node,
-                                double* __restrict__ U, int64_t N, int m, int64_t capL, int64_t capN) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    int32_t n = leaf_node[r];
-    for (int i = 0; i < m; i++) U[i * capL + r] = V[i * capN + n];
+// The new tree's values in one cooperative launch: levels 0 .. J top-down
+// with a grid barrier between levels (a new node is predicted from the new
+// tree's level j - 1), then the leaves gathered into the state array.  L
+// holds the new tree's node offsets.
+template <int D>
+__global__ void k_new_values_all(const uint32_t* __restrict__ code, int J, const int32_t* __restrict__ dmap_old,
+                                 const int32_t* __restrict__ dmap_new, Level L, const double* __restrict__ Vold,
+                                 double* __restrict__ Vnew, int m, int64_t capN,
+                                 const int32_t* __restrict__ leaf_node, double* __restrict__ U, int64_t N,
+                                 int64_t capL, DevCounters* dc) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j <= J; j++) {
+    for (int64_t n = L.noff[j] + tid; n < L.noff[j + 1]; n += nth)
+      new_value_node<D>(code, n, j, dmap_old, dmap_new, L, Vold, Vnew, m, capN, dc);
+    grid.sync();
+  }
+  for (int64_t r = tid; r < N; r += nth) {
+    const int32_t n = leaf_node[r];
+    for (int i = 0; i < m; i++) U[i * capL + r] = Vnew[i * capN + n];
   }
 }
 
@@ -953,21 +987,31 @@ mr_status set_leaves(mr_ctx* c, int64_t n, const uint64_t* keys_dev, const doubl
   return c->hc.status ? MR_EINVAL : MR_OK;
 }
 
-// project the current leaves to all nodes: V = leaf values, then bottom-up means
-static void project(mr_ctx* c, const TreeBuf& t) {
-  k_scatter_leaves<<<grid_for(t.nleaves), kBlock, 0, c->stream>>>(t.U, t.leaf_node, c->V, t.nleaves,
-                                                                  c->m, c->cap_leaves, c->cap_nodes);
+// One cooperative launch of kern (every block co-resident, for its grid
+// barriers): as many kBlock-thread blocks as fit on the device, at most 8 per
+// SM, no more than the work needs.
+template <typename... Args>
+static mr_status coop_launch(mr_ctx* c, void (*kern)(Args...), int64_t work, Args... args) {
+  int dev = 0, nsm = 152, per_sm = 0;
+  MR_CUDA(c, cudaGetDevice(&dev));
+  MR_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  MR_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+  if (per_sm < 1) return MR_ECUDA;
+  const int64_t want = std::max<int64_t>(1, (work + kBlock - 1) / kBlock);
+  const int grid = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 8));
+  void* a[] = {(void*)&args...};
+  MR_CUDA(c, cudaLaunchCooperativeKernel((const void*)kern, grid, kBlock, a, 0, c->stream));
   c->launches++;
-  for (int j = c->J - 1; j >= 0; j--) {
-    int64_t lo = t.noff[j], hi = t.noff[j + 1];
-    if (c->d == 2)
-      k_project_level<2><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(c->V, t.first_child, lo, hi,
-                                                                       c->m, c->cap_nodes);
-    else
-      k_project_level<3><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(c->V, t.first_child, lo, hi,
-                                                                       c->m, c->cap_nodes);
-    c->launches++;
-  }
+  return MR_OK;
+}
+
+// project the current leaves to all nodes: V = leaf values, then bottom-up means
+static mr_status project(mr_ctx* c, const TreeBuf& t) {
+  const Level L = make_level(c, t);
+  const auto kern = c->d == 2 ? k_project_all<2> : k_project_all<3>;
+  return coop_launch(c, kern, std::max<int64_t>(t.nleaves, t.noff[c->J] - t.noff[c->J - 1]),
+                     (const double*)t.U, (const int32_t*)t.leaf_node, c->V, (const int32_t*)t.first_child, L, c->J,
+                     (int64_t)t.nleaves, c->m, c->cap_leaves, c->cap_nodes);
 }
 
 mr_status adapt(mr_ctx* c, double eta) {
@@ -980,7 +1024,7 @@ mr_status adapt(mr_ctx* c, double eta) {
   TreeBuf& t = c->tb[src];
   Level L = make_level(c, t);
   MR_CUDA(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(int), c->stream));
-  project(c, t);
+  MR_TRY(project(c, t));
   // scales s_i = max over leaves |u_i|
   MR_CUDA(c, cudaMemsetAsync(c->dc->scale_bits, 0, sizeof(c->dc->scale_bits), c->stream));
   k_scale<<<grid_for(t.nleaves), kBlock, 0, c->stream>>>(t.U, t.nleaves, m, c->cap_leaves,
@@ -1006,36 +1050,23 @@ mr_status adapt(mr_ctx* c, double eta) {
   // flags and the level sweep
   MR_CUDA(c, cudaMemsetAsync(c->fl_state, 0, c->cap_dense_int, c->stream));
   MR_CUDA(c, cudaMemsetAsync(c->fl_forced, 0, c->cap_dense_int, c->stream));
-  k_flags_init<<<grid_for(t.noff[J]), kBlock, 0, c->stream>>>(t.code, t.lvl, t.first_child, c->tag, L,
-                                                             t.noff[J], J, c->fl_state);
-  c->launches++;
-  for (int i = J - 1; i >= 0; i--) {
-    if (D == 2)
-      k_sweep_level<2><<<grid_for(c->n_level[i]), kBlock, 0, c->stream>>>(c->fl_state, c->fl_forced,
-                                                                          c->fl_final, L, i, c->jmin);
-    else
-      k_sweep_level<3><<<grid_for(c->n_level[i]), kBlock, 0, c->stream>>>(c->fl_state, c->fl_forced,
-                                                                          c->fl_final, L, i, c->jmin);
-    c->launches++;
+  {
+    const auto kern = D == 2 ? k_sweep_all<2> : k_sweep_all<3>;
+    MR_TRY(coop_launch(c, kern, std::max<int64_t>(t.noff[J], c->n_level[J - 1]), (const uint32_t*)t.code,
+                       (const uint8_t*)t.lvl, (const int32_t*)t.first_child, (const uint8_t*)c->tag, L,
+                       (int64_t)t.noff[J], J, c->jmin, c->fl_state, c->fl_forced, c->fl_final));
   }
   mr_status s = tree_from_final(c, dst, true);
   if (s) return s;
   TreeBuf& nt = c->tb[dst];
   Level Ln = make_level(c, nt);
-  for (int j = 0; j <= J; j++) {
-    int64_t lo = nt.noff[j], hi = nt.noff[j + 1];
-    if (hi <= lo) continue;
-    if (D == 2)
-      k_new_values<2><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(nt.code, lo, hi, j, t.dmap, nt.dmap, Ln,
-                                                                   c->V, c->Vnew, m, c->cap_nodes, c->dc);
-    else
-      k_new_values<3><<<grid_for(hi - lo), kBlock, 0, c->stream>>>(nt.code, lo, hi, j, t.dmap, nt.dmap, Ln,
-                                                                   c->V, c->Vnew, m, c->cap_nodes, c->dc);
-    c->launches++;
+  {
+    const auto kern = D == 2 ? k_new_values_all<2> : k_new_values_all<3>;
+    MR_TRY(coop_launch(c, kern, std::max<int64_t>(nt.nleaves, nt.noff[J + 1] - nt.noff[J]), (const uint32_t*)nt.code,
+                       J, (const int32_t*)t.dmap, (const int32_t*)nt.dmap, Ln, (const double*)c->V, c->Vnew, m,
+                       c->cap_nodes, (const int32_t*)nt.leaf_node, nt.U, (int64_t)nt.nleaves, c->cap_leaves,
+                       c->dc));
   }
-  k_gather_leaves<<<grid_for(nt.nleaves), kBlock, 0, c->stream>>>(c->Vnew, nt.leaf_node, nt.U, nt.nleaves,
-                                                                 m, c->cap_leaves, c->cap_nodes);
-  c->launches++;
   MR_CUDA(c, cudaGetLastError());
   MR_TRY(sync_counts(c));
   if (c->hc.status) {

@@ -242,6 +242,10 @@ mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double a
                       BatchReactScratch& S, double* kernel_ms, unsigned long long* counters);
 void free_batch_scratch(BatchReactScratch& S);
 
+// opforms.cu
+mr_status operator_forms(mr_ctx* c, int reps, double* ms_compact, double* ms_csr, int64_t* csr_nnz,
+                         double* max_rel_diff);
+
 // rock4.cu
 int rock4_coeffs(int s, double* mu, double* nu, double* kap, double* w, double* errc);
 double rock4_ell(int s);

@@ -162,12 +162,22 @@ struct RockCtl {
   int nmax, finished, status, rounds;
   long long steps, rejects, stages, matvecs;
   int smax;
-  double bytes;
+  double bytes, flops;
+};
+
+// Work of one sweep shared by the species (the regular-leaf table, none on the
+// uniform grid, and the merged rows) and the arithmetic of one operator
+// application of one species: (2d + 1) per regular leaf (the neighbour sum
+// and the centre term) and 2 per merged-row entry
+struct SweepWork {
+  double tab_bytes, op_flops;
+  int inc;  // the mixed form (FP32 increments)
 };
 
 struct PersArgs {
   int m, D, nb;
   int J;         // finest level (the uniform-grid form's leaves are all at J)
+  SweepWork work;
   int64_t N, capL;
   double dt, tol, rho;
   double Dc[kMaxM];
@@ -183,9 +193,10 @@ __device__ inline double ell_dev(int s) { return 0.336 * (double)s * s - 2.7; }
 // choose the next step of every species (one thread per block, on the
 // block's copy of the control)
 __device__ void rock_prepare(int m, double dt, const double* Dc, double rho_L, RockCtl& C, int64_t N,
-                             double leafb, bool inc = false) {
+                             const SweepWork& W) {
+  const bool inc = W.inc;
   int nmax = 0, any = 0;
-  double bytes = 0.0;
+  double bytes = 0.0, flops = 0.0;
   for (int i = 0; i < m; i++) {
     if (C.done[i]) continue;
     if (C.h[i] <= 1e-14 * dt) {
@@ -226,11 +237,16 @@ __device__ void rock_prepare(int m, double dt, const double* Dc, double rho_L, R
       bytes += N * (28.0 + (s >= 6 ? 12.0 + 16.0 * (s - 6) : 0.0) + 72.0 + 24.0);
     else
       bytes += N * (24.0 * (s - 4) + 112.0 + 32.0);
+    // n + 4 operator applications (stages 2..n, Horner, estimate) and the
+    // combinations per leaf: stages 5 each, Horner 3 + 3 + 8 + 4, estimate 8,
+    // first stage 3
+    flops += (s - 4 + 4) * W.op_flops + N * (5.0 * (s - 5) + 29.0);
     any = 1;
   }
   C.nmax = nmax;
-  // neighbour tables: one gather sweep per stage 2..n and per finishing sweep
-  C.bytes += bytes + (double)(nmax - 1 + 5) * leafb;
+  // tables and merged rows: one gather sweep per stage 2..n and per finishing sweep
+  C.bytes += bytes + (double)(nmax - 1 + 5) * W.tab_bytes;
+  C.flops += flops;
   if (!any) C.finished = 1;
 }
 
@@ -402,7 +418,6 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
   const int64_t tid = (threadIdx.x & 31) + 32 * (blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5)),
                 nth = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  const double leafb = CM ? 0.0 : N * (8.0 * D + 1.0);  // table bytes per sweep (none on the uniform grid)
   // vector q of species i: FP64: the state U (pool 0), W0..W2 (pool 1..3),
   // W3 (error accumulator), W4, W5 (L y); FP32: twelve float vectors carved
   // from the six work buffers, pool 0..3 = vectors 0..3 (vector 0 holds a
@@ -655,7 +670,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
     }
   };
   __syncthreads();
-  if (threadIdx.x == 0) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, leafb, !kF64);
+  if (threadIdx.x == 0) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, P.work);
   __syncthreads();
   bool first = true;
   for (int round = 0; round < 20000; round++) {
@@ -777,7 +792,7 @@ __global__ void __launch_bounds__(kBlock, M > 4 ? 1 : 2)
         C.h[i] *= fac;
       }
       C.rounds++;
-      if (!C.finished) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, leafb);
+      if (!C.finished) rock_prepare(P.m, P.dt, P.Dc, P.rho, C, N, P.work);
     }
     __syncthreads();
   }
@@ -826,6 +841,7 @@ struct JInst {
   int slot;
   double rho;
   double Dc[kMaxM];
+  SweepWork work;
 };
 
 struct JArgs {
@@ -1067,10 +1083,19 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
   // the embedded estimate of one leaf: its squared scaled error goes to E2
   auto finish = [&](const Ops<VT>& o, const JInst& I, int sp, int64_t r, VT d, VT ih2, VT beta) {
     if (o.kind == K_FSAL) {
-      const VT Lx = d * ih2;
-      o.lx[r] = Lx;
-      const double ee = (double)(o.acc[r] + o.cl * Lx);
-      const double sc = A.tol + A.tol * fmax(fabs((double)o.yn[r]), fabs((double)o.x[r]));
+      double ee, sc;
+      if constexpr (kF64) {
+        const VT Lx = d * ih2;
+        o.lx[r] = Lx;
+        ee = (double)(o.acc[r] + o.cl * Lx);
+        sc = A.tol + A.tol * fmax(fabs((double)o.yn[r]), fabs((double)o.x[r]));
+      } else {  // increments: L y_{n+1} = g + L Delta, scale from y_n and y_n + Delta
+        const VT ly1 = o.g[r] + d * ih2;
+        o.lx[r] = ly1;
+        ee = (double)(o.acc[r] + o.cl * ly1);
+        const double yv = o.u[r];
+        sc = A.tol + A.tol * fmax(fabs(yv), fabs(yv + (double)o.x[r]));
+      }
       I.E2[(int64_t)sp * I.capL + r] = (ee / sc) * (ee / sc);
     } else {
       double unused = 0.0;
@@ -1267,7 +1292,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
       C.h[sp] *= fac;
     }
     C.rounds++;
-    if (!C.finished) rock_prepare(A.m, A.dt, I.Dc, I.rho, C, I.N, I.N * (8.0 * D + 1.0), !kF64);
+    if (!C.finished) rock_prepare(A.m, A.dt, I.Dc, I.rho, C, I.N, I.work);
   };
   auto publish = [&]() {  // block 0: the flags every block reads after the next barrier
     if (blockIdx.x == 0) {
@@ -1289,7 +1314,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_rock_joint(JArgs A) {
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const JInst& I = A.inst[i];
-      rock_prepare(A.m, A.dt, I.Dc, I.rho, A.ctl[i], I.N, I.N * (8.0 * D + 1.0), !kF64);
+      rock_prepare(A.m, A.dt, I.Dc, I.rho, A.ctl[i], I.N, I.work);
       for (int sp = 0; sp < kMaxM; sp++) {
         int* pt = A.ptr + 5 * (i * kMaxM + sp);
         pt[0] = 0;
@@ -1586,6 +1611,18 @@ static double sweep_bytes(const mr_ctx* c, const StageArgs& A, int64_t N) {
   return N * (per_leaf + 8.0 * c->d + 1.0) + 12.0 * c->stats.irregular_nnz + 8.0 * c->stats.irregular_rows;
 }
 
+// the sweep work of context c's current tree (see SweepWork); cm: the
+// uniform-grid form (no table)
+static SweepWork sweep_work(const mr_ctx* c, bool cm, bool inc) {
+  const double N = (double)c->tb[c->cur].nleaves, nirr = (double)c->stats.irregular_rows,
+               nnz = (double)c->stats.irregular_nnz;
+  SweepWork W;
+  W.tab_bytes = (cm ? 0.0 : (N - nirr) * (8.0 * c->d + 1.0)) + (inc ? 8.0 : 12.0) * nnz + 8.0 * nirr;
+  W.op_flops = (2.0 * c->d + 1.0) * (N - nirr) + 2.0 * nnz;
+  W.inc = inc;
+  return W;
+}
+
 // 1/h_j^2 of every level in constant memory, written once per device
 static std::mutex g_ih2_mu;
 static bool g_ih2_done[256] = {false};
@@ -1767,6 +1804,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
     P.dt = dt;
     P.tol = tol;
     P.rho = c->rho;
+    P.work = sweep_work(c, cm, f32);
     for (int i = 0; i < mw; i++) P.Dc[i] = c->prob.D[w0 + i];
     // the window's species: rows w0.. of the state and of every work buffer
     P.U = c->tb[c->cur].U + (int64_t)w0 * c->cap_leaves;
@@ -1795,6 +1833,7 @@ mr_status diffuse(mr_ctx* c, double dt, double tol) {
     S.rock_kernel_ms += ms;
     S.rock_kernel_launches++;
     S.rock_alg_bytes += hctl.bytes;
+    S.rock_alg_flops += hctl.flops;
     if (hctl.status) {
       c->last_error = "ROCK4 step control failed";
       return (mr_status)hctl.status;
@@ -1861,6 +1900,7 @@ mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStr
     I.nreg = I.N - I.nirr;
     I.slot = c->irr_slot;
     I.rho = c->rho;
+    I.work = sweep_work(c, false, prec != MR_FP64);
     for (int i = 0; i < m; i++) I.Dc[i] = c->prob.D[i];
     off[b + 1] = off[b] + I.nreg;
     off[(n + 1) + b + 1] = off[(n + 1) + b] + I.nirr;
@@ -1939,6 +1979,7 @@ mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStr
     s.rock_matvec = hctl[b].matvecs;
     s.rock_smax = hctl[b].smax;
     s.rock_alg_bytes += hctl[b].bytes;
+    s.rock_alg_flops += hctl[b].flops;
     if (hctl[b].status && !st) {
       cs[b]->last_error = "ROCK4 step control failed";
       st = (mr_status)hctl[b].status;

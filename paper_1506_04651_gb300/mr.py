@@ -46,7 +46,8 @@ class Stats(C.Structure):
                 ("radau_kernel_ms", C.c_double), ("radau_alg_flops", C.c_double),
                 ("radau_kernel_launches", C.c_int64),
                 ("rock_kernel_ms", C.c_double), ("rock_alg_bytes", C.c_double),
-                ("rock_kernel_launches", C.c_int64), ("radau_counters", C.c_int64 * 8)]
+                ("rock_kernel_launches", C.c_int64), ("radau_counters", C.c_int64 * 8),
+                ("rock_alg_flops", C.c_double)]
 
     def as_dict(self):
         out = {}
@@ -82,6 +83,8 @@ def lib():
             "mr_get_complexity": [vp, vp, i64, C.c_int],
             "mr_mass": [vp, dp],
             "mr_apply_operator": [vp, dp, dp, C.c_int, C.POINTER(C.c_double)],
+            "mr_operator_forms": [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), i64p,
+                                  C.POINTER(C.c_double)],
             "mr_rock4_coefficients": [C.c_int, dp, dp, dp, dp, dp, C.POINTER(C.c_double)],
             "mr_last_error": [vp, C.c_char_p, C.c_size_t],
             "mr_fp64_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -276,6 +279,19 @@ class Context:
         self._check(lib().mr_apply_operator(self.h, C.c_void_p(u.ctypes.data), C.c_void_p(out.ctypes.data),
                                             0, C.byref(rho)), "mr_apply_operator")
         return out, rho.value
+
+
+def _operator_forms(self, reps=20):
+    """Mean device time of one application of the leaf operator in its compact
+    form and as a CSR matrix (mr_operator_forms)."""
+    a, b, d = C.c_double(), C.c_double(), C.c_double()
+    nnz = C.c_int64()
+    self._check(lib().mr_operator_forms(self.h, reps, C.byref(a), C.byref(b), C.byref(nnz), C.byref(d)),
+                "mr_operator_forms")
+    return {"ms_compact": a.value, "ms_csr": b.value, "csr_nnz": nnz.value, "max_rel_diff": d.value}
+
+
+Context.operator_forms = _operator_forms
 
 
 def rock4_coefficients(s):
