@@ -106,20 +106,22 @@ def initial_state(w, J=None):
 
 
 def make_context(mr, w, stream, precision=0):
-    """A library context for workload w (BZ, or the network with its reactions set)."""
+    """A library context for workload w (BZ, or the network with its reactions set);
+    w["max_leaves"], when set, caps the leaf capacity (profiling captures that
+    must hold only a few GB on the device)."""
     from paper_1506_04651_gb300 import inputs as I
+    cap = dict(precision=precision, max_leaves=w.get("max_leaves", 0))
     if w.get("model") == "network":
         sp, kf, kb, D = I.network_instance(w["seed"])
-        c = mr.Context(mr.problem(w["d"], w["J"], model="network", D=D, precision=precision), stream=stream)
+        c = mr.Context(mr.problem(w["d"], w["J"], model="network", D=D, **cap), stream=stream)
         c.set_network(sp, kf, kb)
         return c
     if w.get("model") == "ionic":
-        return mr.Context(mr.problem(w["d"], w["J"], model="ionic", D=I.IONIC_D, precision=precision),
-                          stream=stream)
+        return mr.Context(mr.problem(w["d"], w["J"], model="ionic", D=I.IONIC_D, **cap), stream=stream)
     if w.get("model") == "nagumo":
-        return mr.Context(mr.problem(w["d"], w["J"], model="nagumo", params=(I.NAGUMO_K,), D=(I.NAGUMO_D,),
-                                     precision=precision), stream=stream)
-    return mr.Context(mr.problem(w["d"], w["J"], precision=precision), stream=stream)
+        return mr.Context(mr.problem(w["d"], w["J"], model="nagumo", params=(I.NAGUMO_K,), D=(I.NAGUMO_D,), **cap),
+                          stream=stream)
+    return mr.Context(mr.problem(w["d"], w["J"], **cap), stream=stream)
 
 
 def oracle_model(w):
@@ -897,6 +899,9 @@ def main():
     ap.add_argument("--J", type=int, default=0,
                     help="run the workload at another finest level (profiling captures of a smaller case); "
                          "the line's config records it")
+    ap.add_argument("--max-leaves", type=int, default=0,
+                    help="leaf capacity of the context (0: the full finest grid); for profiling captures that "
+                         "must hold only a few GB on the device")
     ap.add_argument("--instances", type=int, default=0,
                     help="batched workload: the first N of its seeded instances (profiling captures of a "
                          "smaller case); the line's config records it")
@@ -914,6 +919,8 @@ def main():
         run_batch(args, b)
         return
     w = WORKLOADS[args.workload]
+    if args.max_leaves:
+        w = dict(w, max_leaves=args.max_leaves)
     if args.J and args.J != w["J"]:
         w = dict(w, J=args.J, oracle_J=min(w.get("oracle_J", args.J), args.J),
                  desc=w["desc"] + f" -- run at finest level J={args.J}")
