@@ -271,12 +271,43 @@ typedef struct {
   int64_t diffuse_launches;    /* joint ROCK4 launches */
 } mr_batch_stats;
 
+/*
+ * The batch's autotuner (no counterpart in the paper; the launch shapes of
+ * the batched form are chosen by timed trials).  The joint Radau5 launch has
+ * four candidate shapes -- 128 or 64 threads per block, cells taken from the
+ * finest level down or in leaf order -- and the joint ROCK4 launch two -- 2
+ * or 1 blocks of 256 threads per SM.  None changes a result (cells are
+ * integrated independently; the joint ROCK4 error norms are summed in fixed
+ * chunks), so tuning is online: the first launches of mr_batch_run /
+ * mr_batch_diffuse try each candidate twice, rank them by algorithmic work
+ * per millisecond (Radau5: FP64 operations as in mr_stats; ROCK4: sweep
+ * bytes), and the fastest is kept.  On by default.
+ *   mr_batch_set_autotune  on = 1 restarts the trials, on = 0 fixes the
+ *                          default shapes (128 threads, finest first; 2
+ *                          blocks per SM); MR_EINVAL otherwise
+ *   mr_batch_tuning        the trial table: one entry per candidate (the
+ *                          four Radau5 shapes, then the two ROCK4 shapes);
+ *                          *n gets the number of entries, MR_ENOMEM if cap
+ *                          is smaller
+ */
+typedef struct {
+  int32_t phase;       /* 0: joint Radau5 launch, 1: joint ROCK4 launch */
+  int32_t block;       /* threads per block */
+  int32_t per_sm;      /* ROCK4: blocks per SM; Radau5: 0 (as many as fit) */
+  int32_t order;       /* Radau5: 1 finest levels first, 0 leaf order */
+  int64_t launches;    /* launches run with this shape */
+  double ms, work, rate; /* their summed device time and algorithmic work, work per ms */
+  int32_t chosen, reserved;
+} mr_tune_entry;
+
 mr_status mr_batch_create(int n, const mr_problem *probs, int threads, mr_batch **out);
 mr_ctx *mr_batch_context(mr_batch *b, int i);
 mr_status mr_batch_run(mr_batch *b, int nsteps, double dt, const double *eta, double rtol, double atol,
                        double rock_tol);
 mr_status mr_batch_diffuse(mr_batch *b, double dt, double tol);
 mr_status mr_batch_get_stats(const mr_batch *b, mr_batch_stats *out);
+mr_status mr_batch_set_autotune(mr_batch *b, int on);
+mr_status mr_batch_tuning(const mr_batch *b, mr_tune_entry *out, int cap, int *n);
 void mr_batch_destroy(mr_batch *b);
 
 /* Checkpoint and resume.  mr_save writes the current leaves to `path`:

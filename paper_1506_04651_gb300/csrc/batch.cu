@@ -84,6 +84,47 @@ class Pool {
   int dev_;
 };
 
+// Online autotuner of one joint launch: its candidate launch shapes are
+// tried in turn on the first real launches (each `reps` times), ranked by
+// algorithmic work per millisecond of device time (the launches differ in
+// their work, so the rate, not the time, is compared), and the fastest is
+// kept from then on.  Only shapes that leave the results unchanged are
+// candidates, so tuning never changes what a run computes.
+struct Tuner {
+  struct Cand {
+    int a, b;  // the shape: (threads per block, queue order) or (blocks per SM, 0)
+    int64_t launches = 0;
+    double ms = 0.0, work = 0.0;
+  };
+  std::vector<Cand> cand;
+  int reps = 2, chosen = -1, next = 0;
+  bool on = true;
+  // the candidate for the next launch
+  int pick() {
+    if (!on) return 0;
+    if (chosen >= 0) return chosen;
+    return next % (int)cand.size();
+  }
+  void record(int k, double ms, double work) {
+    Cand& c = cand[k];
+    c.launches++;
+    c.ms += ms;
+    c.work += work;
+    if (!on || chosen >= 0) return;
+    next++;
+    if (next >= (int)cand.size() * reps) {
+      double best = -1.0;
+      for (int q = 0; q < (int)cand.size(); q++) {
+        const double rate = cand[q].ms > 0.0 ? cand[q].work / cand[q].ms : 0.0;
+        if (rate > best) {
+          best = rate;
+          chosen = q;
+        }
+      }
+    }
+  }
+};
+
 }  // namespace
 }  // namespace mrg
 
@@ -97,6 +138,11 @@ struct mr_batch {
   mrg::Pool* pool = nullptr;
   mrg::BatchReactScratch scratch;
   mrg::BatchRockScratch rscratch;
+  // the joint Radau5 launch: 128 or 64 threads per block x finest levels
+  // first or leaf order (the default first); the joint ROCK4 launch: 2 or 1
+  // blocks per SM
+  mrg::Tuner tune_react{{{128, 1}, {64, 1}, {128, 0}, {64, 0}}};
+  mrg::Tuner tune_diffuse{{{2, 0}, {1, 0}}};
   mr_batch_stats stats;
   const char* last_error = "";
 };
@@ -155,7 +201,11 @@ mr_status react_all(mr_batch* b, double dt, double rtol, double atol) {
   }
   double ms = 0.0;
   unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
-  const mr_status s = react_batch(b->ctx.data(), b->n, dt, rtol, atol, b->stream, b->scratch, &ms, cnt);
+  const int k = b->tune_react.pick();
+  RadauShape shape;
+  shape.block = b->tune_react.cand[k].a;
+  shape.rev = b->tune_react.cand[k].b;
+  const mr_status s = react_batch(b->ctx.data(), b->n, dt, rtol, atol, b->stream, b->scratch, &ms, cnt, shape);
   if (s) return s;
   if (cudaEventRecord(b->ev_joint, b->stream) != cudaSuccess) return MR_ECUDA;
   for (int i = 0; i < b->n; i++)
@@ -174,7 +224,9 @@ mr_status react_all(mr_batch* b, double dt, double rtol, double atol) {
   // algorithmic FP64 operations (radau_work: counted from the kernel's source)
   int64_t cells = 0;
   for (mr_ctx* c : b->ctx) cells += c->tb[c->cur].nleaves;
-  S.radau_alg_flops += radau_alg_flops(radau_work(b->ctx[0]->prob.model, b->ctx[0]->m), cnt, cells);
+  const double work = radau_alg_flops(radau_work(b->ctx[0]->prob.model, b->ctx[0]->m), cnt, cells);
+  S.radau_alg_flops += work;
+  b->tune_react.record(k, ms, work);
   return MR_OK;
 }
 
@@ -194,9 +246,14 @@ mr_status diffuse_all(mr_batch* b, double dt, double tol) {
         cudaStreamWaitEvent(b->stream, b->ev[i], 0) != cudaSuccess)
       return MR_ECUDA;
   }
-  double ms = 0.0;
-  const mr_status s = diffuse_batch(b->ctx.data(), b->n, dt, tol, b->stream, b->rscratch, &ms);
+  double ms = 0.0, bytes0 = 0.0, bytes1 = 0.0;
+  for (mr_ctx* c : b->ctx) bytes0 += c->stats.rock_alg_bytes;
+  const int k = b->tune_diffuse.pick();
+  const mr_status s =
+      diffuse_batch(b->ctx.data(), b->n, dt, tol, b->stream, b->rscratch, &ms, b->tune_diffuse.cand[k].a);
   if (s) return s;
+  for (mr_ctx* c : b->ctx) bytes1 += c->stats.rock_alg_bytes;
+  b->tune_diffuse.record(k, ms, bytes1 - bytes0);
   if (cudaEventRecord(b->ev_joint, b->stream) != cudaSuccess) return MR_ECUDA;
   for (int i = 0; i < b->n; i++)
     if (cudaStreamWaitEvent(b->streams[i], b->ev_joint, 0) != cudaSuccess) return MR_ECUDA;
@@ -341,6 +398,41 @@ mr_status mr_batch_get_stats(const mr_batch* b, mr_batch_stats* out) {
   if (!b || !out) return MR_EINVAL;
   *out = b->stats;
   return MR_OK;
+}
+
+mr_status mr_batch_set_autotune(mr_batch* b, int on) {
+  if (!b || (on != 0 && on != 1)) return MR_EINVAL;
+  for (Tuner* t : {&b->tune_react, &b->tune_diffuse}) {
+    t->on = on != 0;
+    t->chosen = on ? -1 : 0;
+    t->next = 0;
+    for (Tuner::Cand& c : t->cand) c = Tuner::Cand{c.a, c.b};
+  }
+  return MR_OK;
+}
+
+mr_status mr_batch_tuning(const mr_batch* b, mr_tune_entry* out, int cap, int* n) {
+  if (!b || !n || cap < 0 || (cap > 0 && !out)) return MR_EINVAL;
+  int k = 0;
+  const Tuner* ts[2] = {&b->tune_react, &b->tune_diffuse};
+  for (int phase = 0; phase < 2; phase++)
+    for (int q = 0; q < (int)ts[phase]->cand.size(); q++, k++) {
+      if (k >= cap) continue;
+      const Tuner::Cand& c = ts[phase]->cand[q];
+      mr_tune_entry& e = out[k];
+      memset(&e, 0, sizeof e);
+      e.phase = phase;
+      e.block = phase == 0 ? c.a : 256;
+      e.per_sm = phase == 0 ? 0 : c.a;
+      e.order = phase == 0 ? c.b : 0;
+      e.launches = c.launches;
+      e.ms = c.ms;
+      e.work = c.work;
+      e.rate = c.ms > 0.0 ? c.work / c.ms : 0.0;
+      e.chosen = ts[phase]->chosen == q;
+    }
+  *n = k;
+  return k > cap ? MR_ENOMEM : MR_OK;
 }
 
 void mr_batch_destroy(mr_batch* b) {

@@ -988,8 +988,9 @@ mr_status set_leaves(mr_ctx* c, int64_t n, const uint64_t* keys_dev, const doubl
 }
 
 // One cooperative launch of kern (every block co-resident, for its grid
-// barriers): as many kBlock-thread blocks as fit on the device, at most 8 per
-// SM, no more than the work needs.
+// barriers): at most 2 kBlock-thread blocks per SM, no more than the work
+// needs.  A grid barrier costs more with more blocks, and these loops pass
+// one per level over levels that are mostly small.
 template <typename... Args>
 static mr_status coop_launch(mr_ctx* c, void (*kern)(Args...), int64_t work, Args... args) {
   int dev = 0, nsm = 152, per_sm = 0;
@@ -998,7 +999,7 @@ static mr_status coop_launch(mr_ctx* c, void (*kern)(Args...), int64_t work, Arg
   MR_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return MR_ECUDA;
   const int64_t want = std::max<int64_t>(1, (work + kBlock - 1) / kBlock);
-  const int grid = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 8));
+  const int grid = (int)std::min<int64_t>(want, (int64_t)nsm * std::min(per_sm, 2));
   void* a[] = {(void*)&args...};
   MR_CUDA(c, cudaLaunchCooperativeKernel((const void*)kern, grid, kBlock, a, 0, c->stream));
   c->launches++;

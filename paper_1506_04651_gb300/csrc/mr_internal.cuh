@@ -238,8 +238,16 @@ struct BatchReactScratch {
   int cap = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
 };
+// launch shape of the joint Radau5 launch (the batch's autotuner picks it):
+// threads per block (64 or 128) and the queue order (rev: the finest levels
+// first, else leaf order); neither changes a cell's arithmetic
+struct RadauShape {
+  int block = 128;
+  int rev = 1;
+};
 mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double atol, cudaStream_t stream,
-                      BatchReactScratch& S, double* kernel_ms, unsigned long long* counters);
+                      BatchReactScratch& S, double* kernel_ms, unsigned long long* counters,
+                      const RadauShape& shape);
 void free_batch_scratch(BatchReactScratch& S);
 
 // opforms.cu
@@ -264,8 +272,10 @@ struct BatchRockScratch {
   int64_t part_cap = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
 };
+// per_sm: blocks per SM of the cooperative grid (1 or 2; the joint kernel's
+// results do not depend on it: its error norms are summed in fixed chunks)
 mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStream_t stream, BatchRockScratch& S,
-                        double* kernel_ms);
+                        double* kernel_ms, int per_sm = 2);
 void free_batch_rock(BatchRockScratch& S);
 
 }  // namespace mrg

@@ -239,9 +239,13 @@ struct BatchCells {
   BatchInst<Mdl> one;
 };
 
-template <class Mdl, typename LT = double>
-__global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int64_t N, double tend,
-                                               DevCounters* dc) {
+// BS: threads per block; rev: take the cells from the last one down (the
+// finest levels first: leaves are stored level-major, and the finest levels
+// hold the front cells that need the most steps) or in leaf order.  Neither
+// changes a cell's arithmetic.
+template <class Mdl, typename LT = double, int BS = 128>
+__global__ void __launch_bounds__(BS) k_radau(BatchCells<Mdl> B, RadauC C, int64_t N, double tend,
+                                              DevCounters* dc, int rev = 1) {
   constexpr int M = Mdl::M;
   // the instance of the current cell
   Mdl mdl = B.one.md;
@@ -280,9 +284,7 @@ __global__ void __launch_bounds__(128) k_radau(BatchCells<Mdl> B, RadauC C, int6
     if (cell < 0) {
       const unsigned long long ticket = atomicAdd(&dc->work_next, 1ull);
       if (ticket >= (unsigned long long)N) break;
-      // finest leaves first: leaves are stored level-major, and the finest
-      // levels hold the front cells that need the most steps
-      cell = N - 1 - (int64_t)ticket;
+      cell = rev ? N - 1 - (int64_t)ticket : (int64_t)ticket;
       if (B.inst) {
         int lo = 0, hi = B.n - 1;  // last instance with offs[b] <= cell
         while (lo < hi) {
@@ -882,9 +884,9 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
 
 // ------------------------------------------------------------ batched reaction
 namespace {
-template <class Mdl, typename LT>
-mr_status launch_batch(mr_ctx* const* cs, int n, const Mdl* mds, const RadauC& C, double dt, cudaStream_t stream,
-                       BatchReactScratch& S, int64_t total) {
+template <class Mdl, typename LT, int BS>
+mr_status launch_batch_bs(mr_ctx* const* cs, int n, const Mdl* mds, const RadauC& C, double dt, cudaStream_t stream,
+                          BatchReactScratch& S, int64_t total, int rev) {
   std::vector<BatchInst<Mdl>> hin(n);
   for (int b = 0; b < n; b++) {
     TreeBuf& t = cs[b]->tb[cs[b]->cur];
@@ -896,14 +898,21 @@ mr_status launch_batch(mr_ctx* const* cs, int n, const Mdl* mds, const RadauC& C
   int dev = 0, nsm = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radau<Mdl, LT>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radau<Mdl, LT, BS>, BS, 0);
   per_sm = std::max(per_sm, 1);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, (int64_t)nsm * per_sm));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + BS - 1) / BS, (int64_t)nsm * per_sm));
   BatchCells<Mdl> B{reinterpret_cast<const BatchInst<Mdl>*>(S.inst), S.offs, n, hin[0]};
   cudaEventRecord(S.ev[0], stream);
-  k_radau<Mdl, LT><<<grid, 128, 0, stream>>>(B, C, total, dt, S.dc);
+  k_radau<Mdl, LT, BS><<<grid, BS, 0, stream>>>(B, C, total, dt, S.dc, rev);
   cudaEventRecord(S.ev[1], stream);
   return cudaGetLastError() == cudaSuccess ? MR_OK : MR_ECUDA;
+}
+
+template <class Mdl, typename LT>
+mr_status launch_batch(mr_ctx* const* cs, int n, const Mdl* mds, const RadauC& C, double dt, cudaStream_t stream,
+                       BatchReactScratch& S, int64_t total, const RadauShape& shape) {
+  if (shape.block == 64) return launch_batch_bs<Mdl, LT, 64>(cs, n, mds, C, dt, stream, S, total, shape.rev);
+  return launch_batch_bs<Mdl, LT, 128>(cs, n, mds, C, dt, stream, S, total, shape.rev);
 }
 }  // namespace
 
@@ -917,7 +926,8 @@ void free_batch_scratch(BatchReactScratch& S) {
 }
 
 mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double atol, cudaStream_t stream,
-                      BatchReactScratch& S, double* kernel_ms, unsigned long long* counters) {
+                      BatchReactScratch& S, double* kernel_ms, unsigned long long* counters, const RadauShape& shape) {
+  if (shape.block != 64 && shape.block != 128) return MR_EINVAL;
   if (n < 1) return MR_EINVAL;
   const int model = cs[0]->prob.model, prec = cs[0]->prob.precision;
   if (model != MR_MODEL_BZ && model != MR_MODEL_NAGUMO) return MR_EINVAL;
@@ -955,13 +965,13 @@ mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double a
       const double* p = cs[b]->prob.params;
       mds[b] = BZ{1.0 / p[1], 1.0 / p[0], p[2], p[3]};
     }
-    st = mixed ? launch_batch<BZ, float>(cs, n, mds.data(), C, dt, stream, S, total)
-               : launch_batch<BZ, double>(cs, n, mds.data(), C, dt, stream, S, total);
+    st = mixed ? launch_batch<BZ, float>(cs, n, mds.data(), C, dt, stream, S, total, shape)
+               : launch_batch<BZ, double>(cs, n, mds.data(), C, dt, stream, S, total, shape);
   } else {
     std::vector<Nagumo> mds(n);
     for (int b = 0; b < n; b++) mds[b] = Nagumo{cs[b]->prob.params[0]};
-    st = mixed ? launch_batch<Nagumo, float>(cs, n, mds.data(), C, dt, stream, S, total)
-               : launch_batch<Nagumo, double>(cs, n, mds.data(), C, dt, stream, S, total);
+    st = mixed ? launch_batch<Nagumo, float>(cs, n, mds.data(), C, dt, stream, S, total, shape)
+               : launch_batch<Nagumo, double>(cs, n, mds.data(), C, dt, stream, S, total, shape);
   }
   if (st) return st;
   DevCounters hc;

@@ -1864,7 +1864,8 @@ void free_batch_rock(BatchRockScratch& S) {
 }
 
 mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStream_t stream, BatchRockScratch& S,
-                        double* kernel_ms) {
+                        double* kernel_ms, int blocks_per_sm) {
+  if (blocks_per_sm != 1 && blocks_per_sm != 2) return MR_EINVAL;
   if (n < 1) return MR_EINVAL;
   const int m = cs[0]->m, prec = cs[0]->prob.precision;
   if (cs[0]->d != 2 || (m != 1 && m != 3)) return MR_EINVAL;
@@ -1960,7 +1961,7 @@ mr_status diffuse_batch(mr_ctx* const* cs, int n, double dt, double tol, cudaStr
   A.part = S.part;
   A.flags = S.flags;
   void* args[] = {&A};
-  const int nb = nsm * std::min(per_sm, 2);
+  const int nb = nsm * std::min(per_sm, blocks_per_sm);
   cudaEventRecord(S.ev[0], stream);
   if (cudaLaunchCooperativeKernel(kern, nb, kBlock, args, smem, stream) != cudaSuccess) return MR_ECUDA;
   cudaEventRecord(S.ev[1], stream);

@@ -95,6 +95,8 @@ def lib():
             "mr_batch_run": [vp, C.c_int, C.c_double, dp, C.c_double, C.c_double, C.c_double],
             "mr_batch_diffuse": [vp, C.c_double, C.c_double],
             "mr_batch_get_stats": [vp, C.POINTER(BatchStats)],
+            "mr_batch_set_autotune": [vp, C.c_int],
+            "mr_batch_tuning": [vp, vp, C.c_int, C.POINTER(C.c_int)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -110,6 +112,12 @@ def lib():
         L.mr_status_str.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("phase", C.c_int32), ("block", C.c_int32), ("per_sm", C.c_int32), ("order", C.c_int32),
+                ("launches", C.c_int64), ("ms", C.c_double), ("work", C.c_double), ("rate", C.c_double),
+                ("chosen", C.c_int32), ("reserved", C.c_int32)]
 
 
 class BatchStats(C.Structure):
@@ -358,6 +366,22 @@ class Batch:
         s = BatchStats()
         lib().mr_batch_get_stats(self.h, C.byref(s))
         return s.as_dict()
+
+    def set_autotune(self, on):
+        rc = lib().mr_batch_set_autotune(self.h, int(bool(on)))
+        if rc:
+            raise MRError(rc, "mr_batch_set_autotune")
+
+    def tuning(self):
+        """The autotuner's trial table: one dict per candidate launch shape."""
+        arr = (TuneEntry * 16)()
+        n = C.c_int()
+        rc = lib().mr_batch_tuning(self.h, C.addressof(arr), 16, C.byref(n))
+        if rc:
+            raise MRError(rc, "mr_batch_tuning")
+        names = ("reaction", "diffusion")
+        return [dict(phase=names[e.phase], block=e.block, per_sm=e.per_sm, order=e.order, launches=e.launches,
+                     ms=e.ms, work=e.work, rate=e.rate, chosen=bool(e.chosen)) for e in arr[:n.value]]
 
     def close(self):
         if getattr(self, "h", None):

@@ -174,3 +174,36 @@ def test_full_batch_config_one_step(mr):
         for i in range(3):
             assert np.max(np.abs(v_g[i] - v_o[i])) <= 1e-9 * np.max(np.abs(v_o[i]))
     b.close()
+
+
+def test_autotuner_changes_no_result(mr):
+    """The batch's autotuner tries its candidate launch shapes on the first
+    launches (joint Radau5: 128 or 64 threads per block, finest levels first
+    or leaf order; joint ROCK4: 2 or 1 blocks per SM).  None of them changes
+    a result: after six steps every instance equals, bit for bit, the same
+    batch run with the default shapes fixed.  The trial table lists every
+    candidate, each tried twice, and one shape chosen per phase."""
+    insts = instances(6)
+    eta = [i["eta"] for i, _ in insts]
+    runs = []
+    for tuned in (True, False):
+        b = mr.Batch([problem(mr, i) for i, _ in insts], threads=4)
+        if not tuned:
+            b.set_autotune(False)
+        for k, (inst, u0) in enumerate(insts):
+            b[k].build(u0, inst["eta"])
+        b.run(6, 1e-3, eta)
+        runs.append(([b[k].leaves() for k in range(b.n)], b.tuning()))
+        b.close()
+    (tuned, table), (fixed, table_fixed) = runs
+    for (k1, v1), (k2, v2) in zip(tuned, fixed):
+        assert np.array_equal(k1, k2) and np.array_equal(v1, v2)
+    react = [e for e in table if e["phase"] == "reaction"]
+    diff = [e for e in table if e["phase"] == "diffusion"]
+    assert len(react) == 4 and len(diff) == 2
+    assert all(e["launches"] >= 2 and e["rate"] > 0 for e in react + diff)
+    assert sum(e["chosen"] for e in react) == 1 and sum(e["chosen"] for e in diff) == 1
+    assert {(e["block"], e["order"]) for e in react} == {(128, 1), (64, 1), (128, 0), (64, 0)}
+    assert {e["per_sm"] for e in diff} == {1, 2}
+    # with the tuner off only the default shapes run
+    assert [e["launches"] > 0 for e in table_fixed] == [True, False, False, False, True, False]
