@@ -765,13 +765,16 @@ def run_batch(args, b):
 
     def make(prec):
         B = mr.Batch([mr.problem(2, inst["J"], params=(1e-2, 1e-5, inst["f"], 2e-3), precision=prec)
-                      for inst in insts])
+                      for inst in insts], threads=args.threads)
         for k, inst in enumerate(insts):
             B[k].build(torch.from_numpy(u0s[k]).to(dev), inst["eta"])
         return B
 
     B = make(mr.MR_FP64)
-    B.run(args.warmup, b["dt"], eta, TOL, TOL, TOL)
+    # at least 4 warm-up steps: the autotuner's trials (4 Radau5 shapes and 2
+    # ROCK4 shapes, each twice) are then over before the timed steps
+    warm = max(args.warmup, 4)
+    B.run(warm, b["dt"], eta, TOL, TOL, TOL)
     start = [B[k].leaves() for k in range(B.n)]  # the timed steps' starting state, for the e2e replay
     launches0 = sum(B[k].stats()["kernel_launches"] for k in range(B.n))
     clocks = ClockSampler(local)
@@ -781,6 +784,7 @@ def run_batch(args, b):
     torch.cuda.synchronize()
     clk = clocks.stop()
     st = B.stats()
+    tuning = B.tuning()  # the autotuner's trials (made during the warm-up steps) and its choice
     launches = sum(B[k].stats()["kernel_launches"] for k in range(B.n)) - launches0 + st["react_launches"]
     ms = st["ms_device"]
     value = st["leaf_updates"] / (ms * 1e-3)
@@ -837,7 +841,7 @@ def run_batch(args, b):
     mixed = None
     if not args.no_mixed:
         Bm = make(mr.MR_MIXED)
-        Bm.run(args.warmup, b["dt"], eta, TOL, TOL, TOL)
+        Bm.run(warm, b["dt"], eta, TOL, TOL, TOL)
         Bm.run(args.steps, b["dt"], eta, TOL, TOL, TOL)
         sm = Bm.stats()
         errs, errs_same, flipped = [], [], []
@@ -868,7 +872,7 @@ def run_batch(args, b):
         Bm.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": b["desc"], "instances": len(insts),
@@ -876,6 +880,9 @@ def run_batch(args, b):
                        "leaves_total_last_step": sum(len(f[0]) for f in final64),
                        "l2": "inputs larger than L2 (all instances' state and work vectors)"},
             "roofline": roof, "e2e": e2e, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
+            "autotuner": {"trials": tuning,
+                          "note": "launch shapes tried on the first launches (each twice), ranked by algorithmic "
+                                  "work per ms; none changes a result"},
             "mixed": mixed, "kernels": {"joint_radau": {"ms": st["ms_react_kernel"], "launches": st["react_launches"],
                                                        "tflops": ach},
                                         "phases_ms_per_step": {"adapt_and_tables": st["ms_adapt_phase"] / args.steps,
@@ -902,6 +909,9 @@ def main():
     ap.add_argument("--max-leaves", type=int, default=0,
                     help="leaf capacity of the context (0: the full finest grid); for profiling captures that "
                          "must hold only a few GB on the device")
+    ap.add_argument("--threads", type=int, default=0,
+                    help="batched workload: host threads driving the instances' adaptation (0: the library's "
+                         "default, one per core up to 32)")
     ap.add_argument("--instances", type=int, default=0,
                     help="batched workload: the first N of its seeded instances (profiling captures of a "
                          "smaller case); the line's config records it")

@@ -81,6 +81,7 @@ mr_status alloc_all(mr_ctx* c) {
   int64_t big = std::max(std::max(c->cap_dense_int, c->cap_nodes), c->cap_leaves);
   A(c->scan_tmp, 2 * (big / 2048 + 4));
   A(c->itmp, std::max(c->cap_nodes, 2 * c->cap_leaves + 2));
+  A(c->level_new, mrg::kMaxL + 2);
   A(c->nbr, (int64_t)2 * d * c->cap_leaves);
   A(c->leaf_lvl, c->cap_leaves);
   A(c->irr_leaf, c->cap_leaves);
@@ -116,7 +117,7 @@ void free_all(mr_ctx* c) {
   }
   cudaFree(c->V); cudaFree(c->Vnew); cudaFree(c->fl_state); cudaFree(c->fl_forced);
   cudaFree(c->fl_final); cudaFree(c->grank); cudaFree(c->tag); cudaFree(c->smap); cudaFree(c->scan_tmp);
-  cudaFree(c->itmp); cudaFree(c->nbr); cudaFree(c->leaf_lvl); cudaFree(c->irr_leaf); cudaFree(c->reg_tab);
+  cudaFree(c->itmp); cudaFree(c->level_new); cudaFree(c->nbr); cudaFree(c->leaf_lvl); cudaFree(c->irr_leaf); cudaFree(c->reg_tab);
   cudaFree(c->irr_cnt); cudaFree(c->irr_ptr); cudaFree(c->irr_col); cudaFree(c->irr_w); cudaFree(c->irr_wf); cudaFree(c->e2buf);
   for (int q = 0; q < 6; q++) cudaFree(c->work[q]);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->complexity); cudaFree(c->dc);

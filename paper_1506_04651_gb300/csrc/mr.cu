@@ -54,6 +54,11 @@ struct Level {
   int64_t noff[kMaxL + 2];
 };
 
+// thresholds eps_j = 2^((d/2)(j - J)) eta of every level, computed on the host
+struct Thresholds {
+  double eps[kMaxL + 1];
+};
+
 // ------------------------------------------------------------ projection
 // parent = mean of its 2^d children, summed in child order (Sec. 2.2)
 template <int D>
@@ -144,8 +149,8 @@ __device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 template <int D, typename DT = double>
 __global__ void k_details(const double* __restrict__ V, const uint32_t* __restrict__ code,
                           const uint8_t* __restrict__ lvl, const int32_t* __restrict__ dmap,
-                          Level L, int64_t nnodes, int m, int64_t capN, const double* __restrict__ scale,
-                          const double* __restrict__ eps_j, uint8_t* __restrict__ tag,
+                          Level L, int64_t nnodes, int m, int64_t capN,
+                          const unsigned long long* __restrict__ scale_bits, Thresholds T, uint8_t* __restrict__ tag,
                           double* __restrict__ delta_out, DevCounters* dc) {
   // the 3^d prediction weights of each child parity, built in the order
   // predict() multiplies them (they are products of 1 and +-1/8, exact)
@@ -162,6 +167,9 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
     }
     sw[par][q % NST] = (DT)w;  // a product of 1 and +-1/8: exact in float too
   }
+  // s_i = max(max over leaves |u_i|, 1e-30), from the ordered bits k_scale left
+  __shared__ double s_scale[kMaxM];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s_scale[i] = fmax(__longlong_as_double(scale_bits[i]), 1e-30);
   __syncthreads();
   for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nnodes;
        n += (int64_t)gridDim.x * blockDim.x) {
@@ -195,13 +203,13 @@ __global__ void k_details(const double* __restrict__ V, const uint32_t* __restri
         DT p = DT(0);  // same products and sums, in the same order, as predict()
 #pragma unroll
         for (int o = 0; o < NST; o++) p = add_rn(p, mul_rn(sw[parity][o], (DT)Vi[idx[o]]));
-        const DT dd = fabs(add_rn((DT)Vi[n], -p)) / (DT)scale[i];
+        const DT dd = fabs(add_rn((DT)Vi[n], -p)) / (DT)s_scale[i];
         finite = finite && isfinite(dd);
         dmax = fmax(dmax, (double)dd);
       }
     }
     if (isnan(dmax) || !finite) atomicCAS(&dc->status, 0, (int)MR_ESTATE);
-    tag[n] = dmax >= eps_j[j];
+    tag[n] = dmax >= T.eps[j];
     if (delta_out) delta_out[n] = dmax;
   }
 }
@@ -367,24 +375,38 @@ __device__ inline void new_value_node(const uint32_t* __restrict__ code, int64_t
   }
 }
 
-// The new tree's values in one cooperative launch: levels 0 .. J top-down
-// with a grid barrier between levels (a new node is predicted from the new
-// tree's level j - 1), then the leaves gathered into the state array.  L
-// holds the new tree's node offsets.
+// The new tree's values in one cooperative launch.  Every node that the old
+// tree had copies its value at once (no order needed); the nodes the
+// adaptation created are listed per level and predicted level by level from
+// the new tree's level j - 1 (1 .. J, a grid barrier between levels), then the
+// leaves are gathered into the state array.  L holds the new tree's node
+// offsets; list has room for every node; level_new starts at zero.
 template <int D>
-__global__ void k_new_values_all(const uint32_t* __restrict__ code, int J, const int32_t* __restrict__ dmap_old,
-                                 const int32_t* __restrict__ dmap_new, Level L, const double* __restrict__ Vold,
-                                 double* __restrict__ Vnew, int m, int64_t capN,
+__global__ void k_new_values_all(const uint32_t* __restrict__ code, const uint8_t* __restrict__ lvl, int J,
+                                 const int32_t* __restrict__ dmap_old, const int32_t* __restrict__ dmap_new, Level L,
+                                 const double* __restrict__ Vold, double* __restrict__ Vnew, int m, int64_t capN,
                                  const int32_t* __restrict__ leaf_node, double* __restrict__ U, int64_t N,
-                                 int64_t capL, DevCounters* dc) {
+                                 int64_t capL, int32_t* __restrict__ list, int32_t* __restrict__ level_new,
+                                 DevCounters* dc) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j <= J; j++) {
-    for (int64_t n = L.noff[j] + tid; n < L.noff[j + 1]; n += nth)
-      new_value_node<D>(code, n, j, dmap_old, dmap_new, L, Vold, Vnew, m, capN, dc);
-    grid.sync();
+  for (int64_t n = tid; n < L.noff[J + 1]; n += nth) {
+    const int j = lvl[n];
+    const int32_t o = dmap_old[L.doff[j] + code[n]];
+    if (o >= 0) {
+      for (int i = 0; i < m; i++) Vnew[i * capN + n] = Vold[i * capN + o];
+    } else {
+      list[L.noff[j] + atomicAdd(&level_new[j], 1)] = (int32_t)n;
+    }
   }
+  for (int j = 1; j <= J; j++) {
+    grid.sync();
+    const int cnt = __ldcg(&level_new[j]);
+    for (int64_t q = tid; q < cnt; q += nth)
+      new_value_node<D>(code, list[L.noff[j] + q], j, dmap_old, dmap_new, L, Vold, Vnew, m, capN, dc);
+  }
+  grid.sync();
   for (int64_t r = tid; r < N; r += nth) {
     const int32_t n = leaf_node[r];
     for (int i = 0; i < m; i++) U[i * capL + r] = Vnew[i * capN + n];
@@ -1031,22 +1053,15 @@ mr_status adapt(mr_ctx* c, double eta) {
   k_scale<<<grid_for(t.nleaves), kBlock, 0, c->stream>>>(t.U, t.nleaves, m, c->cap_leaves,
                                                           c->dc->scale_bits);
   c->launches++;
-  MR_TRY(sync_counts(c));
-  double hs[kMaxM + kMaxL + 2];
-  for (int i = 0; i < m; i++) {
-    double s;
-    memcpy(&s, &c->hc.scale_bits[i], sizeof s);
-    hs[i] = fmax(s, 1e-30);
-  }
-  for (int j = 0; j <= J; j++) hs[kMaxM + j] = eta * pow(2.0, 0.5 * D * (j - J));
-  if (c->hc.status) return (mr_status)c->hc.status;
-  double* dpar = c->red_out;  // small device parameter block
-  MR_CUDA(c, cudaMemcpyAsync(dpar, hs, sizeof(double) * (kMaxM + J + 1), cudaMemcpyHostToDevice, c->stream));
+  // the details kernel reads the scales from the device; the thresholds
+  // depend on eta, d and J only (no host round trip)
+  Thresholds th;
+  for (int j = 0; j <= kMaxL; j++) th.eps[j] = j <= J ? eta * pow(2.0, 0.5 * D * (j - J)) : 0.0;
   const bool f32d = c->prob.precision == MR_MIXED_F32_DETAILS;
   const auto details = D == 2 ? (f32d ? k_details<2, float> : k_details<2, double>)
                               : (f32d ? k_details<3, float> : k_details<3, double>);
   details<<<grid_for(t.nnodes), kBlock, 0, c->stream>>>(c->V, t.code, t.lvl, t.dmap, L, t.nnodes, m, c->cap_nodes,
-                                                        dpar, dpar + kMaxM, c->tag, nullptr, c->dc);
+                                                        c->dc->scale_bits, th, c->tag, nullptr, c->dc);
   c->launches++;
   // flags and the level sweep
   MR_CUDA(c, cudaMemsetAsync(c->fl_state, 0, c->cap_dense_int, c->stream));
@@ -1062,11 +1077,12 @@ mr_status adapt(mr_ctx* c, double eta) {
   TreeBuf& nt = c->tb[dst];
   Level Ln = make_level(c, nt);
   {
+    MR_CUDA(c, cudaMemsetAsync(c->level_new, 0, sizeof(int32_t) * (kMaxL + 2), c->stream));
     const auto kern = D == 2 ? k_new_values_all<2> : k_new_values_all<3>;
-    MR_TRY(coop_launch(c, kern, std::max<int64_t>(nt.nleaves, nt.noff[J + 1] - nt.noff[J]), (const uint32_t*)nt.code,
-                       J, (const int32_t*)t.dmap, (const int32_t*)nt.dmap, Ln, (const double*)c->V, c->Vnew, m,
-                       c->cap_nodes, (const int32_t*)nt.leaf_node, nt.U, (int64_t)nt.nleaves, c->cap_leaves,
-                       c->dc));
+    MR_TRY(coop_launch(c, kern, std::max<int64_t>(nt.nleaves, nt.noff[J + 1]), (const uint32_t*)nt.code,
+                       (const uint8_t*)nt.lvl, J, (const int32_t*)t.dmap, (const int32_t*)nt.dmap, Ln,
+                       (const double*)c->V, c->Vnew, m, c->cap_nodes, (const int32_t*)nt.leaf_node, nt.U,
+                       (int64_t)nt.nleaves, c->cap_leaves, c->itmp, c->level_new, c->dc));
   }
   MR_CUDA(c, cudaGetLastError());
   MR_TRY(sync_counts(c));

@@ -147,6 +147,7 @@ struct mr_ctx {
   uint8_t* tag = nullptr;            // per node tag of the last detail pass
   int32_t* scan_tmp = nullptr;       // block partials for scans
   int32_t* itmp = nullptr;           // int scratch [cap_nodes]
+  int32_t* level_new = nullptr;      // [kMaxL + 2] per level: nodes an adaptation created
   // leaf operator tables
   int32_t* nbr = nullptr;            // [2d][cap_leaves]
   uint8_t* leaf_lvl = nullptr;
