@@ -521,8 +521,10 @@ def run_gpu(args, w):
     if not args.no_mixed:
         mixed = run_mixed(args, w, mr, torch, dev, stream, u0)
     hbm_point = None
+    extras = None
     if args.workload == DEFAULT and not args.no_hbm_extra and not args.J:
         hbm_point = run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf)
+        extras = run_extras(args, mr, torch, dev, stream, fp64_tf, hbm)
     if pg:
         pg.barrier()
     if rank != 0:
@@ -565,7 +567,7 @@ def run_gpu(args, w):
                        "leaves_last_step": st["leaves"], "compression_ratio": st["compression_ratio"],
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roof, "roofline_rock4": roof_rock, "roofline_adapt": roof_adapt, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "mixed": mixed, "hbm_point": hbm_point,
+            "gpu_launches": launches, "clocks": clk, "mixed": mixed, "hbm_point": hbm_point, "extras": extras,
             "operator_forms": forms,
             "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
     if conservation:
@@ -633,61 +635,121 @@ def rock_roofline(nbytes, flops, ms, hbm, fp64_tf, mixed_form):
 def run_hbm_point(mr, torch, dev, stream, hbm, fp64_tf, steps=3, warmup=2):
     """The HBM-resident point of the 3D BZ workload (J = 9, 512^3 finest,
     leaf vectors larger than L2) as a bounded extra of the default line: a
-    few CUDA-event-timed steps with the L2 flushed before each, and the
-    rooflines of its ROCK4 sweeps (bytes against HBM) and its adaptation."""
+    few CUDA-event-timed steps with the L2 flushed before each, in the FP64
+    and the mixed form, and the rooflines of its ROCK4 sweeps (against
+    min(HBM, the FP64 pipe at their intensity) in FP64, against HBM in the
+    mixed form), its Radau5 launches and its adaptation."""
     w = WORKLOADS["bz3d_J9_eta1e-2"]
     t0 = time.perf_counter()
-    u0 = torch.from_numpy(initial_state(w)).to(dev)
-    ctx = make_context(mr, w, stream)
-    ctx.build(u0, w["eta"])
-    del u0
-    for _ in range(warmup):
-        ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    st0 = ctx.stats()
-    ms, leaves, nodes = 0.0, 0, 0
-    ph = {"adapt_and_tables": 0.0, "react_both_halves": 0.0, "diffuse": 0.0}
-    for _ in range(steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
-        e1.record(stream)
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
-        sk = ctx.stats()
-        leaves += sk["leaves"]
-        nodes += sk["nodes"]
-        ph["adapt_and_tables"] += sk["ms_adapt"]
-        ph["react_both_halves"] += sk["ms_react"]
-        ph["diffuse"] += sk["ms_diffuse"]
-    st1 = ctx.stats()
-    forms = ctx.operator_forms(reps=20)
-    ctx.close()
+    u0 = initial_state(w)
     peak = hbm or 6800.0
-    rock_ms = st1["rock_kernel_ms"] - st0["rock_kernel_ms"]
-    rock_b = st1["rock_alg_bytes"] - st0["rock_alg_bytes"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    forms = {}
+    out = {"workload": "bz3d_J9_eta1e-2", "desc": w["desc"], "steps": steps, "warmup": warmup, "unit": UNIT,
+           "l2": "flushed before every timed step (256 MB write); state and work vectors exceed L2"}
+    for prec, tag in ((mr.MR_FP64, "fp64"), (mr.MR_MIXED, "mixed")):
+        ctx = make_context(mr, w, stream, precision=prec)
+        ctx.build(torch.from_numpy(u0).to(dev), w["eta"])
+        for _ in range(warmup):
+            ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+        st0 = ctx.stats()
+        ms, leaves, nodes = 0.0, 0, 0
+        ph = {"adapt_and_tables": 0.0, "react_both_halves": 0.0, "diffuse": 0.0}
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            sk = ctx.stats()
+            leaves += sk["leaves"]
+            nodes += sk["nodes"]
+            ph["adapt_and_tables"] += sk["ms_adapt"]
+            ph["react_both_halves"] += sk["ms_react"]
+            ph["diffuse"] += sk["ms_diffuse"]
+        st1 = ctx.stats()
+        if prec == mr.MR_FP64:
+            forms = ctx.operator_forms(reps=20)
+        ctx.close()
+        rock_ms = st1["rock_kernel_ms"] - st0["rock_kernel_ms"]
+        rock = rock_roofline(st1["rock_alg_bytes"] - st0["rock_alg_bytes"],
+                             st1["rock_alg_flops"] - st0["rock_alg_flops"], rock_ms, hbm, fp64_tf,
+                             mixed_form=prec != mr.MR_FP64)
+        rock["ms_per_launch"] = rock_ms / max(1, st1["rock_kernel_launches"] - st0["rock_kernel_launches"])
+        rad_ms = st1["radau_kernel_ms"] - st0["radau_kernel_ms"]
+        rad_fl = st1["radau_alg_flops"] - st0["radau_alg_flops"]
+        adapt_ms = ph["adapt_and_tables"] / steps
+        adapt_b = 2.0 * (nodes / steps) * (8.0 * 3 + 6.0)
+        rec = {"value": leaves / (ms * 1e-3), "ms_per_step": ms / steps, "leaves_last_step": st1["leaves"],
+               "irregular_rows": st1["irregular_rows"], "irregular_nnz": st1["irregular_nnz"],
+               "phase_ms_per_step": {k: v / steps for k, v in ph.items()}, "roofline_rock4": rock,
+               "roofline_adapt": {"bound": "hbm", "achieved": adapt_b / (adapt_ms * 1e-3) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": adapt_b / (adapt_ms * 1e-3) / 1e9 / peak}}
+        if prec == mr.MR_FP64:
+            rec["roofline_radau"] = {"bound": "alu", "achieved": rad_fl / (rad_ms * 1e-3) / 1e12, "peak": fp64_tf,
+                                     "unit": "TFLOP/s", "frac": rad_fl / (rad_ms * 1e-3) / 1e12 / fp64_tf}
+            out.update(rec)
+        else:
+            rec["speedup_vs_fp64"] = rec["value"] / out["value"]
+            out["mixed"] = rec
+    out["operator_forms"] = dict(forms, ratio_compact_over_csr=forms["ms_compact"] / forms["ms_csr"],
+                                 paper_ratio_3d="0.67 (BZ 3D J=10, 40 Haswell threads, App. C Table 5)")
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def run_extras(args, mr, torch, dev, stream, fp64_tf, hbm):
+    """Bounded extras of the default line, so that one run of the default
+    bench also measures the 3D J = 7 workload (cfg 3) and the 64-instance
+    batch (cfg 4): a few CUDA-event-timed steps each, the L2 flushed before
+    each 3D step, FP64 and the mixed form."""
+    out = {}
+    w = WORKLOADS["bz3d_J7_eta1e-2"]
+    u0 = initial_state(w)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    for prec in (mr.MR_FP64, mr.MR_MIXED):
+        c = make_context(mr, w, stream, precision=prec)
+        c.build(torch.from_numpy(u0).to(dev), w["eta"])
+        for _ in range(3):
+            c.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+        st0 = c.stats()
+        ms, leaves = 0.0, 0
+        for _ in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.strang(w["dt"], w["eta"], TOL, TOL, TOL)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            leaves += c.stats()["leaves"]
+        st1 = c.stats()
+        res[prec] = (leaves / (ms * 1e-3), ms / 5, c.leaves(), st0, st1)
+        c.close()
+    v64, ms64, (kf, vf), st0, st1 = res[mr.MR_FP64]
     rad_ms = st1["radau_kernel_ms"] - st0["radau_kernel_ms"]
     rad_fl = st1["radau_alg_flops"] - st0["radau_alg_flops"]
-    adapt_ms = ph["adapt_and_tables"] / steps
-    adapt_b = 2.0 * (nodes / steps) * (8.0 * 3 + 6.0)
-    return {"workload": "bz3d_J9_eta1e-2", "desc": w["desc"], "steps": steps, "warmup": warmup,
-            "value": leaves / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
-            "leaves_last_step": st1["leaves"], "irregular_rows": st1["irregular_rows"],
-            "irregular_nnz": st1["irregular_nnz"],
-            "phase_ms_per_step": {k: v / steps for k, v in ph.items()},
-            "roofline_rock4": dict(rock_roofline(rock_b, st1["rock_alg_flops"] - st0["rock_alg_flops"], rock_ms,
-                                                 hbm, fp64_tf, mixed_form=False),
-                                   ms_per_launch=rock_ms / max(1, st1["rock_kernel_launches"] -
-                                                               st0["rock_kernel_launches"])),
-            "roofline_adapt": {"bound": "hbm", "achieved": adapt_b / (adapt_ms * 1e-3) / 1e9, "peak": peak,
-                               "unit": "GB/s", "frac": adapt_b / (adapt_ms * 1e-3) / 1e9 / peak},
-            "roofline_radau": {"bound": "alu", "achieved": rad_fl / (rad_ms * 1e-3) / 1e12, "peak": fp64_tf,
-                               "unit": "TFLOP/s", "frac": rad_fl / (rad_ms * 1e-3) / 1e12 / fp64_tf},
-            "l2": "flushed before every timed step (256 MB write); state and work vectors exceed L2",
-            "operator_forms": dict(forms, ratio_compact_over_csr=forms["ms_compact"] / forms["ms_csr"],
-                                   paper_ratio_3d="0.67 (BZ 3D J=10, 40 Haswell threads, App. C Table 5)"),
-            "wall_s": time.perf_counter() - t0}
+    out["bz3d_J7_eta1e-2"] = {
+        "desc": w["desc"], "steps": 5, "warmup": 3, "value": v64, "unit": UNIT, "ms_per_step": ms64,
+        "leaves_last_step": st1["leaves"],
+        "roofline_radau": {"bound": "alu", "achieved": rad_fl / (rad_ms * 1e-3) / 1e12, "peak": fp64_tf,
+                           "unit": "TFLOP/s", "frac": rad_fl / (rad_ms * 1e-3) / 1e12 / fp64_tf},
+        "roofline_rock4": rock_roofline(st1["rock_alg_bytes"] - st0["rock_alg_bytes"],
+                                        st1["rock_alg_flops"] - st0["rock_alg_flops"],
+                                        st1["rock_kernel_ms"] - st0["rock_kernel_ms"], hbm, fp64_tf, False),
+        "mixed": {"value": res[mr.MR_MIXED][0], "speedup_vs_fp64": res[mr.MR_MIXED][0] / v64,
+                  "rel_l1_vs_fp64_path": rel_l1_finest(*res[mr.MR_MIXED][2], kf, vf, w["d"], w["J"])},
+        "l2": "flushed before every timed step"}
+    del flush
+    bargs = argparse.Namespace(**dict(vars(args), steps=3, warmup=4, no_mixed=False, threads=0, instances=0))
+    line = run_batch(bargs, BATCH["batch64_bz2d"], print_line=False)
+    out["batch64_bz2d"] = {k: line[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "roofline",
+                                                "mixed", "autotuner", "kernels", "e2e", "gpu_launches")}
+    out["batch64_bz2d"]["desc"] = BATCH["batch64_bz2d"]["desc"]
+    return out
 
 
 def run_mixed(args, w, mr, torch, dev, stream, u0):
@@ -745,7 +807,7 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
             "_final": {"fp64": (kf, vf), "mixed": (km, vm), "f32_details": (kd, vd)}}
 
 
-def run_batch(args, b):
+def run_batch(args, b, print_line=True):
     """Batched serving workload through the native batch (mr_batch_*): every
     instance adapts and diffuses on its own stream, the reaction half steps of
     all instances are joint Radau5 launches.  value = leaves of all instances
@@ -888,8 +950,9 @@ def run_batch(args, b):
                                         "phases_ms_per_step": {"adapt_and_tables": st["ms_adapt_phase"] / args.steps,
                                                                "react_joint": st["ms_react_kernel"] / args.steps,
                                                                "diffuse": st["ms_diffuse_phase"] / args.steps}}}
-    if rank == 0:
+    if rank == 0 and print_line:
         print(json.dumps(line), flush=True)
+    return line
 
 
 def main():

@@ -85,11 +85,14 @@ class Pool {
 };
 
 // Online autotuner of one joint launch: its candidate launch shapes are
-// tried in turn on the first real launches (each `reps` times), ranked by
-// algorithmic work per millisecond of device time (the launches differ in
-// their work, so the rate, not the time, is compared), and the fastest is
-// kept from then on.  Only shapes that leave the results unchanged are
-// candidates, so tuning never changes what a run computes.
+// tried in turn on the first real launches, each for `reps` consecutive
+// launches, ranked by algorithmic work per millisecond of device time (the
+// launches differ in their work, so the rate, not the time, is compared),
+// and the fastest is kept from then on.  The reaction's two half steps of a
+// Strang step differ systematically (after the adaptation, after the
+// diffusion), so with reps = 2 every candidate sees one of each.  Only shapes
+// that leave the results unchanged are candidates, so tuning never changes
+// what a run computes.
 struct Tuner {
   struct Cand {
     int a, b;  // the shape: (threads per block, queue order) or (blocks per SM, 0)
@@ -103,7 +106,7 @@ struct Tuner {
   int pick() {
     if (!on) return 0;
     if (chosen >= 0) return chosen;
-    return next % (int)cand.size();
+    return (next / reps) % (int)cand.size();
   }
   void record(int k, double ms, double work) {
     Cand& c = cand[k];
