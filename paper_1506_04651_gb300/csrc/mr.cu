@@ -378,7 +378,8 @@ __device__ inline void new_value_node(const uint32_t* __restrict__ code, int64_t
 // The new tree's values in one cooperative launch.  Every node that the old
 // tree had copies its value at once (no order needed); the nodes the
 // adaptation created are listed per level and predicted level by level from
-// the new tree's level j - 1 (1 .. J, a grid barrier between levels), then the
+// the new tree's level j - 1 (1 .. J, a grid barrier after every level that
+// has any), then the
 // leaves are gathered into the state array.  L holds the new tree's node
 // offsets; list has room for every node; level_new starts at zero.
 template <int D>
@@ -400,13 +401,17 @@ __global__ void k_new_values_all(const uint32_t* __restrict__ code, const uint8_
       list[L.noff[j] + atomicAdd(&level_new[j], 1)] = (int32_t)n;
     }
   }
+  grid.sync();
+  // the per-level counts are final now and read alike by every thread, so
+  // levels without created nodes cost no barrier (usually all but the finest
+  // one or two)
   for (int j = 1; j <= J; j++) {
-    grid.sync();
     const int cnt = __ldcg(&level_new[j]);
+    if (cnt == 0) continue;
     for (int64_t q = tid; q < cnt; q += nth)
       new_value_node<D>(code, list[L.noff[j] + q], j, dmap_old, dmap_new, L, Vold, Vnew, m, capN, dc);
+    grid.sync();
   }
-  grid.sync();
   for (int64_t r = tid; r < N; r += nth) {
     const int32_t n = leaf_node[r];
     for (int i = 0; i < m; i++) U[i * capL + r] = Vnew[i * capN + n];
