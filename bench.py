@@ -569,6 +569,7 @@ def run_gpu(args, w):
             "roofline": roof, "roofline_rock4": roof_rock, "roofline_adapt": roof_adapt, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "mixed": mixed, "hbm_point": hbm_point, "extras": extras,
             "operator_forms": forms,
+            "cm_over_mr_step_time": (extras["bz2d_J10_cm"]["ms_per_step"] / (ms / args.steps)) if extras else None,
             "fp64_probe": {"tflops": fp64_tf, "sm_mhz_attr": fp64_mhz}}
     if conservation:
         line["conservation"] = conservation
@@ -743,6 +744,28 @@ def run_extras(args, mr, torch, dev, stream, fp64_tf, hbm):
         "mixed": {"value": res[mr.MR_MIXED][0], "speedup_vs_fp64": res[mr.MR_MIXED][0] / v64,
                   "rel_l1_vs_fp64_path": rel_l1_finest(*res[mr.MR_MIXED][2], kf, vf, w["d"], w["J"])},
         "l2": "flushed before every timed step"}
+    # the uniform 1024^2 grid of the same fronts (Cartesian mesh, eta = 0):
+    # the CM side of the paper's MR-versus-CM comparison (Tables 1-2)
+    wc = WORKLOADS["bz2d_J10_cm"]
+    c = make_context(mr, wc, stream)
+    c.build(torch.from_numpy(initial_state(wc)).to(dev), wc["eta"])
+    for _ in range(3):
+        c.strang(wc["dt"], wc["eta"], TOL, TOL, TOL)
+    ms = 0.0
+    for _ in range(5):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.strang(wc["dt"], wc["eta"], TOL, TOL, TOL)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    cells = c.stats()["leaves"]
+    c.close()
+    out["bz2d_J10_cm"] = {"desc": wc["desc"], "steps": 5, "warmup": 3, "value": cells * 5 / (ms * 1e-3),
+                          "unit": "cell-updates/s", "ms_per_step": ms / 5,
+                          "note": "ms_per_step against the default line's adaptive step gives the CM/MR step-time "
+                                  "ratio (the paper: 4.4 for BZ 2D J=10 on 40 Haswell threads, Table 1)"}
     del flush
     bargs = argparse.Namespace(**dict(vars(args), steps=3, warmup=4, no_mixed=False, threads=0, instances=0))
     line = run_batch(bargs, BATCH["batch64_bz2d"], print_line=False)
