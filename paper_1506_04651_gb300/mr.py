@@ -280,6 +280,15 @@ class Context:
         self._check(lib().mr_mass(self.h, C.c_void_p(out.ctypes.data)), "mr_mass")
         return out
 
+    def operator_forms(self, reps=20):
+        """Mean device time of one application of the leaf operator in its compact
+        form and as a CSR matrix (mr_operator_forms)."""
+        a, b, d = C.c_double(), C.c_double(), C.c_double()
+        nnz = C.c_int64()
+        self._check(lib().mr_operator_forms(self.h, reps, C.byref(a), C.byref(b), C.byref(nnz), C.byref(d)),
+                    "mr_operator_forms")
+        return {"ms_compact": a.value, "ms_csr": b.value, "csr_nnz": nnz.value, "max_rel_diff": d.value}
+
     def apply_operator(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.zeros_like(u)
@@ -287,19 +296,6 @@ class Context:
         self._check(lib().mr_apply_operator(self.h, C.c_void_p(u.ctypes.data), C.c_void_p(out.ctypes.data),
                                             0, C.byref(rho)), "mr_apply_operator")
         return out, rho.value
-
-
-def _operator_forms(self, reps=20):
-    """Mean device time of one application of the leaf operator in its compact
-    form and as a CSR matrix (mr_operator_forms)."""
-    a, b, d = C.c_double(), C.c_double(), C.c_double()
-    nnz = C.c_int64()
-    self._check(lib().mr_operator_forms(self.h, reps, C.byref(a), C.byref(b), C.byref(nnz), C.byref(d)),
-                "mr_operator_forms")
-    return {"ms_compact": a.value, "ms_csr": b.value, "csr_nnz": nnz.value, "max_rel_diff": d.value}
-
-
-Context.operator_forms = _operator_forms
 
 
 def rock4_coefficients(s):
