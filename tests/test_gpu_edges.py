@@ -114,3 +114,32 @@ def test_step_arguments_rejected(mr):
     with pytest.raises(mr.MRError) as e:
         c.strang(1e-3, 1e-3, rtol=0.0)
     assert e.value.code == -1
+
+
+def test_capacities_and_empty_inputs_are_reported(mr):
+    """Capacity and size errors reach the caller before any data is written:
+    a leaf capacity below the finest grid makes mr_build report MR_ENOMEM, a
+    short output buffer makes mr_get_leaves report MR_ENOMEM with the count
+    it needs, and an empty or non-tiling leaf set is MR_EINVAL."""
+    import ctypes as C
+    small = mr.Context(mr.problem(2, 6, max_leaves=100))
+    with pytest.raises(mr.MRError) as e:
+        small.build(I.bz_front_2d(6, 1), 1e-3)
+    assert e.value.code == -2
+    c = mr.Context(mr.problem(2, 6))
+    c.build(I.bz_front_2d(6, 1), 1e-3)
+    n = c.num_leaves()
+    keys = np.zeros(n, dtype=np.uint64)
+    vals = np.zeros((3, n))
+    got = C.c_int64()
+    rc = mr.lib().mr_get_leaves(c.h, C.c_void_p(keys.ctypes.data), C.c_void_p(vals.ctypes.data), n - 1,
+                                C.byref(got), 0)
+    assert rc == -2 and got.value == n
+    assert not keys.any() and not vals.any()  # nothing written
+    with pytest.raises(mr.MRError) as e:
+        c.set_leaves(np.zeros(0, dtype=np.uint64), np.zeros((3, 0)))
+    assert e.value.code == -1
+    k, v = c.leaves()
+    with pytest.raises(mr.MRError) as e:  # one leaf missing: the leaves no longer tile the domain
+        c.set_leaves(k[:-1].copy(), np.ascontiguousarray(v[:, :-1]))
+    assert e.value.code == -1

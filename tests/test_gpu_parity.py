@@ -14,6 +14,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_1506_04651_gb300 import inputs as I
+from tests import gridcmp as G
 
 pytestmark = pytest.mark.gpu
 
@@ -265,10 +266,13 @@ def test_nagumo_front_trajectory_matches_oracle(mr, d, J, eta):
     assert T.adapt(eta) == 0 and Tp.adapt(eta) == 0
     ctx = gpu_ctx(mr, d, J, model="nagumo")
     ctx.build(u0, eta)
+    cmx = gpu_ctx(mr, d, J, model="nagumo", precision=mr.MR_MIXED)
+    cmx.build(u0, eta)
     for s in range(5):
         assert T.strang(md, [I.NAGUMO_D], 1e-2, eta) == 0
         assert Tp.strang(md, [I.NAGUMO_D], 1e-2, eta) == 0
         ctx.strang(1e-2, eta)
+        cmx.strang(1e-2, eta)
         k_o, v_o = T.leaves()
         k_p, v_p = Tp.leaves()
         k_g, v_g = ctx.leaves()
@@ -276,6 +280,9 @@ def test_nagumo_front_trajectory_matches_oracle(mr, d, J, eta):
         assert np.array_equal(k_o, k_p), s
         spread = rel_linf(v_p, v_o)
         assert rel_linf(v_g, v_o) <= max(1e-9 * (s + 1), 20.0 * spread), (s, spread)
+    # the mixed form (FP32 increments in up to ~80 ROCK4 stages) at the end
+    k_m, v_m = cmx.leaves()
+    assert G.rel_l1_finest(k_m, v_m, k_o, v_o, d, J) <= 1e-5
 
 
 @pytest.mark.parametrize("d,J", [(2, 9), (3, 6)])
