@@ -425,10 +425,10 @@ def run_gpu(args, w):
         ach = rad_fl / (rad_ms * 1e-3) / 1e12
         kname = ("k_radau_team (Radau5, one 16-lane team per cell, FP64)" if w.get("model") == "network"
                  else "k_radau_team (Radau5, one warp per cell, numerical Jacobian, FP64)"
-                 if w.get("model") == "ionic" else "k_radau (Radau5, FP64)")
+                 if w.get("model") == "ionic" else "k_radau_pool (Radau5, phase-sorted cell pool, FP64)")
         roof = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": fp64_tf,
                 "unit": "TFLOP/s", "frac": ach / fp64_tf,
-                "traffic": profiled_traffic("radau5.cu", "k_radau_bz2d_J10.md")
+                "traffic": profiled_traffic("radau5.cu", "k_radau_pool_bz2d_J10.md")
                 if args.workload == DEFAULT else None,
                 "peak_source": "measured FP64 FMA rate of this GPU (library probe, 2 flop/FMA)",
                 "launches": rad_n, "ms_per_launch": rad_ms / max(rad_n, 1)}
@@ -875,7 +875,10 @@ def run_batch(args, b, print_line=True):
     value = st["leaf_updates"] / (ms * 1e-3)
     fp64_tf, _ = mr.fp64_fma_rate()
     ach = st["radau_alg_flops"] / (st["ms_react_kernel"] * 1e-3) / 1e12 if st["ms_react_kernel"] else 0.0
-    roof = {"bound": "alu", "kernel": "k_radau (joint Radau5 launch over all instances, FP64)", "achieved": ach,
+    chosen = [e for e in tuning if e["phase"] == "reaction" and e["chosen"]]
+    kname = ("k_radau_pool" if not chosen or chosen[0]["schedule"] == "pool" else "k_radau")
+    roof = {"bound": "alu", "kernel": kname + " (joint Radau5 launch over all instances, the autotuner's shape, FP64)",
+            "achieved": ach,
             "peak": fp64_tf, "unit": "TFLOP/s", "frac": ach / fp64_tf, "traffic": None,
             "peak_source": "measured FP64 FMA rate of this GPU (library probe, 2 flop/FMA)",
             "launches": st["react_launches"], "ms_per_launch": st["ms_react_kernel"] / max(st["react_launches"], 1)}

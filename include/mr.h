@@ -57,6 +57,7 @@ typedef enum {
 
 enum { MR_MODEL_BZ = 1, MR_MODEL_NAGUMO = 2, MR_MODEL_NETWORK = 3, MR_MODEL_IONIC = 4 };
 enum { MR_FP64 = 0, MR_MIXED = 1, MR_MIXED_F32_DETAILS = 2 };
+enum { MR_RADAU_THREAD = 0, MR_RADAU_POOL = 1 };
 
 #define MR_MAX_SPECIES 32
 #define MR_IONIC_SPECIES 21
@@ -203,6 +204,20 @@ mr_status mr_adapt(mr_ctx *ctx, double eta);
  * whose reactions are not set. */
 mr_status react_radau5(mr_ctx *ctx, double dt, double rtol, double atol);
 
+/* Schedule of the Radau5 launches of BZ and NAGUMO contexts (the network
+ * and membrane models have their team kernels only):
+ *   MR_RADAU_THREAD  one thread integrates one cell at a time, taking cells
+ *                    from a device work queue; a pass is one step attempt;
+ *   MR_RADAU_POOL    the cells in flight are held in a shared-memory pool per
+ *                    SM, and each warp runs one phase of a step attempt
+ *                    (prepare: Jacobian, factorisations, starting values; one
+ *                    Newton iteration; error estimate and step control) for
+ *                    up to 32 cells that are in that phase.
+ * Both run the same operations per cell in the same order, so results and
+ * complexity counts are bit-identical.  New contexts use MR_RADAU_POOL.
+ * MR_EINVAL for another value. */
+mr_status mr_set_radau_schedule(mr_ctx *ctx, int schedule);
+
 /* Diffusion sub-step D_dt (Sec. 2.1, Sec. 3.2.1): every species integrates
  * u' = D_i L u with the ROCK4-type stabilized method (tol > 0).  Species
  * with D_i = 0 are left unchanged.  MR_EINVAL for dt <= 0 or tol <= 0;
@@ -283,10 +298,14 @@ typedef struct {
  * per millisecond (Radau5: FP64 operations as in mr_stats; ROCK4: sweep
  * bytes), and the fastest is kept.  On by default.
  *   mr_batch_set_autotune  on = 1 restarts the trials, on = 0 fixes the
- *                          default shapes (128 threads, finest first; 2
- *                          blocks per SM); MR_EINVAL otherwise
+ *                          default shapes (the pooled Radau5 schedule,
+ *                          finest first; 2 blocks per SM); MR_EINVAL
+ *                          otherwise
  *   mr_batch_tuning        the trial table: one entry per candidate (the
- *                          four Radau5 shapes, then the two ROCK4 shapes);
+ *                          six Radau5 shapes: the pooled schedule in both
+ *                          queue orders, the thread schedule with 128 or 64
+ *                          threads per block in both; then the two ROCK4
+ *                          shapes);
  *                          *n gets the number of entries, MR_ENOMEM if cap
  *                          is smaller
  */
@@ -297,7 +316,8 @@ typedef struct {
   int32_t order;       /* Radau5: 1 finest levels first, 0 leaf order */
   int64_t launches;    /* launches run with this shape */
   double ms, work, rate; /* their summed device time and algorithmic work, work per ms */
-  int32_t chosen, reserved;
+  int32_t chosen;
+  int32_t schedule;    /* Radau5: MR_RADAU_THREAD or MR_RADAU_POOL (block 128 = 4 warps per SM) */
 } mr_tune_entry;
 
 mr_status mr_batch_create(int n, const mr_problem *probs, int threads, mr_batch **out);

@@ -95,7 +95,8 @@ class Pool {
 // what a run computes.
 struct Tuner {
   struct Cand {
-    int a, b;  // the shape: (threads per block, queue order) or (blocks per SM, 0)
+    int a, b;   // the shape: (threads per block, queue order) or (blocks per SM, 0)
+    int c = 0;  // Radau5 schedule (MR_RADAU_THREAD or MR_RADAU_POOL)
     int64_t launches = 0;
     double ms = 0.0, work = 0.0;
   };
@@ -141,10 +142,16 @@ struct mr_batch {
   mrg::Pool* pool = nullptr;
   mrg::BatchReactScratch scratch;
   mrg::BatchRockScratch rscratch;
-  // the joint Radau5 launch: 128 or 64 threads per block x finest levels
-  // first or leaf order (the default first); the joint ROCK4 launch: 2 or 1
-  // blocks per SM
-  mrg::Tuner tune_react{{{128, 1}, {64, 1}, {128, 0}, {64, 0}}};
+  // the joint Radau5 launch: the pooled schedule, or the thread schedule
+  // with 128 or 64 threads per block, each with the finest levels first or
+  // in leaf order (the default first); the joint ROCK4 launch: 2 or 1 blocks
+  // per SM
+  mrg::Tuner tune_react{{{128, 1, MR_RADAU_POOL},
+                         {128, 0, MR_RADAU_POOL},
+                         {128, 1, MR_RADAU_THREAD},
+                         {64, 1, MR_RADAU_THREAD},
+                         {128, 0, MR_RADAU_THREAD},
+                         {64, 0, MR_RADAU_THREAD}}};
   mrg::Tuner tune_diffuse{{{2, 0}, {1, 0}}};
   mr_batch_stats stats;
   const char* last_error = "";
@@ -208,6 +215,7 @@ mr_status react_all(mr_batch* b, double dt, double rtol, double atol) {
   RadauShape shape;
   shape.block = b->tune_react.cand[k].a;
   shape.rev = b->tune_react.cand[k].b;
+  shape.pool = b->tune_react.cand[k].c == MR_RADAU_POOL;
   const mr_status s = react_batch(b->ctx.data(), b->n, dt, rtol, atol, b->stream, b->scratch, &ms, cnt, shape);
   if (s) return s;
   if (cudaEventRecord(b->ev_joint, b->stream) != cudaSuccess) return MR_ECUDA;
@@ -409,7 +417,7 @@ mr_status mr_batch_set_autotune(mr_batch* b, int on) {
     t->on = on != 0;
     t->chosen = on ? -1 : 0;
     t->next = 0;
-    for (Tuner::Cand& c : t->cand) c = Tuner::Cand{c.a, c.b};
+    for (Tuner::Cand& c : t->cand) c = Tuner::Cand{c.a, c.b, c.c};
   }
   return MR_OK;
 }
@@ -433,6 +441,7 @@ mr_status mr_batch_tuning(const mr_batch* b, mr_tune_entry* out, int cap, int* n
       e.work = c.work;
       e.rate = c.ms > 0.0 ? c.work / c.ms : 0.0;
       e.chosen = ts[phase]->chosen == q;
+      e.schedule = phase == 0 ? c.c : 0;
     }
   *n = k;
   return k > cap ? MR_ENOMEM : MR_OK;

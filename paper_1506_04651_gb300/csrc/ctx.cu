@@ -119,6 +119,7 @@ void free_all(mr_ctx* c) {
   cudaFree(c->fl_final); cudaFree(c->grank); cudaFree(c->tag); cudaFree(c->smap); cudaFree(c->scan_tmp);
   cudaFree(c->itmp); cudaFree(c->level_new); cudaFree(c->nbr); cudaFree(c->leaf_lvl); cudaFree(c->irr_leaf); cudaFree(c->reg_tab);
   cudaFree(c->irr_cnt); cudaFree(c->irr_ptr); cudaFree(c->irr_col); cudaFree(c->irr_w); cudaFree(c->irr_wf); cudaFree(c->e2buf);
+  cudaFree(c->radau_pool);
   for (int q = 0; q < 6; q++) cudaFree(c->work[q]);
   cudaFree(c->red); cudaFree(c->red_out); cudaFree(c->complexity); cudaFree(c->dc);
   cudaFree(c->rho_bits);
@@ -391,6 +392,12 @@ mr_status mr_adapt(mr_ctx* c, double eta) {
   mr_status s = adapt(c, eta);
   if (!s) refresh_tree_stats(c);
   return s;
+}
+
+mr_status mr_set_radau_schedule(mr_ctx* c, int schedule) {
+  if (check_ctx(c) || (schedule != MR_RADAU_THREAD && schedule != MR_RADAU_POOL)) return MR_EINVAL;
+  c->radau_schedule = schedule;
+  return MR_OK;
 }
 
 mr_status react_radau5(mr_ctx* c, double dt, double rtol, double atol) {

@@ -176,6 +176,9 @@ struct mr_ctx {
   cudaEvent_t ev[8];
   cudaEvent_t tev[2 * 256];           // per-launch timing pairs of the ROCK4 sweeps
   mr_stats stats;
+  int radau_schedule = MR_RADAU_POOL;  // Radau5 schedule of BZ and NAGUMO contexts
+  void* radau_pool = nullptr;          // slot data of the pooled Radau5 kernel (lazy)
+  size_t radau_pool_bytes = 0;
   int64_t launches = 0;
   std::string last_error;
   // radau constants (host-computed, passed by value to kernels)
@@ -238,6 +241,8 @@ struct BatchReactScratch {
   int64_t* offs = nullptr;  // prefix offsets of the instances' leaf counts (device)
   int cap = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  void* pool = nullptr;     // slot data of the pooled Radau5 kernel (lazy)
+  size_t pool_bytes = 0;
 };
 // launch shape of the joint Radau5 launch (the batch's autotuner picks it):
 // threads per block (64 or 128) and the queue order (rev: the finest levels
@@ -245,6 +250,7 @@ struct BatchReactScratch {
 struct RadauShape {
   int block = 128;
   int rev = 1;
+  int pool = 0;  // 1: the pooled kernel (4 warps per block; block ignored)
 };
 mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double atol, cudaStream_t stream,
                       BatchReactScratch& S, double* kernel_ms, unsigned long long* counters,

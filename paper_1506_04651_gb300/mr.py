@@ -17,6 +17,7 @@ MR_OK = 0
 MR_MODEL_BZ, MR_MODEL_NAGUMO, MR_MODEL_NETWORK, MR_MODEL_IONIC = 1, 2, 3, 4
 IONIC_SPECIES = 21
 MR_FP64, MR_MIXED, MR_MIXED_F32_DETAILS = 0, 1, 2
+MR_RADAU_THREAD, MR_RADAU_POOL = 0, 1
 MAX_SPECIES, MAX_LEVEL = 32, 16
 NOALLOC_MAX_CELLS = 2147483647  # MR_NOALLOC_MAX_CELLS of include/mr.h
 
@@ -77,6 +78,7 @@ def lib():
             "mr_get_leaves": [vp, vp, dp, i64, i64p, C.c_int],
             "mr_adapt": [vp, C.c_double],
             "react_radau5": [vp, C.c_double, C.c_double, C.c_double],
+            "mr_set_radau_schedule": [vp, C.c_int],
             "diffuse_rock4": [vp, C.c_double, C.c_double],
             "strang_step": [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double],
             "mr_get_stats": [vp, C.POINTER(Stats)],
@@ -117,7 +119,7 @@ def lib():
 class TuneEntry(C.Structure):
     _fields_ = [("phase", C.c_int32), ("block", C.c_int32), ("per_sm", C.c_int32), ("order", C.c_int32),
                 ("launches", C.c_int64), ("ms", C.c_double), ("work", C.c_double), ("rate", C.c_double),
-                ("chosen", C.c_int32), ("reserved", C.c_int32)]
+                ("chosen", C.c_int32), ("schedule", C.c_int32)]
 
 
 class BatchStats(C.Structure):
@@ -241,6 +243,10 @@ class Context:
 
     def react(self, dt, rtol=1e-6, atol=1e-6):
         return self._check(lib().react_radau5(self.h, dt, rtol, atol), "react_radau5")
+
+    def set_radau_schedule(self, schedule):
+        """MR_RADAU_POOL (the default) or MR_RADAU_THREAD; bit-identical results."""
+        return self._check(lib().mr_set_radau_schedule(self.h, schedule), "mr_set_radau_schedule")
 
     def diffuse(self, dt, tol=1e-6):
         return self._check(lib().diffuse_rock4(self.h, dt, tol), "diffuse_rock4")
@@ -377,7 +383,8 @@ class Batch:
             raise MRError(rc, "mr_batch_tuning")
         names = ("reaction", "diffusion")
         return [dict(phase=names[e.phase], block=e.block, per_sm=e.per_sm, order=e.order, launches=e.launches,
-                     ms=e.ms, work=e.work, rate=e.rate, chosen=bool(e.chosen)) for e in arr[:n.value]]
+                     ms=e.ms, work=e.work, rate=e.rate, chosen=bool(e.chosen),
+                     schedule="pool" if e.schedule == MR_RADAU_POOL else "thread") for e in arr[:n.value]]
 
     def close(self):
         if getattr(self, "h", None):

@@ -178,8 +178,9 @@ def test_full_batch_config_one_step(mr):
 
 def test_autotuner_changes_no_result(mr):
     """The batch's autotuner tries its candidate launch shapes on the first
-    launches (joint Radau5: 128 or 64 threads per block, finest levels first
-    or leaf order; joint ROCK4: 2 or 1 blocks per SM).  None of them changes
+    launches (joint Radau5: the pooled schedule, or the thread schedule with
+    128 or 64 threads per block, each with the finest levels first or in leaf
+    order; joint ROCK4: 2 or 1 blocks per SM).  None of them changes
     a result: after six steps every instance equals, bit for bit, the same
     batch run with the default shapes fixed.  The trial table lists every
     candidate, each tried twice, and one shape chosen per phase."""
@@ -200,10 +201,12 @@ def test_autotuner_changes_no_result(mr):
         assert np.array_equal(k1, k2) and np.array_equal(v1, v2)
     react = [e for e in table if e["phase"] == "reaction"]
     diff = [e for e in table if e["phase"] == "diffusion"]
-    assert len(react) == 4 and len(diff) == 2
+    assert len(react) == 6 and len(diff) == 2
     assert all(e["launches"] >= 2 and e["rate"] > 0 for e in react + diff)
     assert sum(e["chosen"] for e in react) == 1 and sum(e["chosen"] for e in diff) == 1
-    assert {(e["block"], e["order"]) for e in react} == {(128, 1), (64, 1), (128, 0), (64, 0)}
+    assert {(e["schedule"], e["block"], e["order"]) for e in react} == {
+        ("pool", 128, 1), ("pool", 128, 0), ("thread", 128, 1), ("thread", 64, 1), ("thread", 128, 0),
+        ("thread", 64, 0)}
     assert {e["per_sm"] for e in diff} == {1, 2}
     # with the tuner off only the default shapes run
-    assert [e["launches"] > 0 for e in table_fixed] == [True, False, False, False, True, False]
+    assert [e["launches"] > 0 for e in table_fixed] == [True] + [False] * 5 + [True, False]
