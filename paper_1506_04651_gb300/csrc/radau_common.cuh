@@ -32,12 +32,12 @@ __device__ inline double root4(double x) { return sqrt(sqrt(x)); }
 // within a few ulps of pow at a fraction of its FP64 instructions (the factor
 // only enters the comparison with the Newton tolerance)
 __device__ inline double pow08(double x) {
-  double y = (double)exp2f(0.8f * log2f((float)x));
+  double y = (double)exp2f(__fmul_rn(0.8f, log2f((float)x)));
   const double x2 = x * x, x4 = x2 * x2;
 #pragma unroll
   for (int q = 0; q < 2; q++) {
     const double y2 = y * y;
-    y = y + (x4 / (y2 * y2) - y) * 0.2;
+    y = fma(x4 / (y2 * y2) - y, 0.2, y);
   }
   return y;
 }
