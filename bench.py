@@ -105,6 +105,10 @@ def initial_state(w, J=None):
     return I.bz_sphere_3d(J, w["seed"])
 
 
+# Radau5 schedule of BZ and NAGUMO contexts (None: the library's default, one thread per cell)
+RADAU_SCHEDULE = None
+
+
 def make_context(mr, w, stream, precision=0):
     """A library context for workload w (BZ, or the network with its reactions set);
     w["max_leaves"], when set, caps the leaf capacity (profiling captures that
@@ -119,9 +123,13 @@ def make_context(mr, w, stream, precision=0):
     if w.get("model") == "ionic":
         return mr.Context(mr.problem(w["d"], w["J"], model="ionic", D=I.IONIC_D, **cap), stream=stream)
     if w.get("model") == "nagumo":
-        return mr.Context(mr.problem(w["d"], w["J"], model="nagumo", params=(I.NAGUMO_K,), D=(I.NAGUMO_D,), **cap),
-                          stream=stream)
-    return mr.Context(mr.problem(w["d"], w["J"], **cap), stream=stream)
+        c = mr.Context(mr.problem(w["d"], w["J"], model="nagumo", params=(I.NAGUMO_K,), D=(I.NAGUMO_D,), **cap),
+                       stream=stream)
+    else:
+        c = mr.Context(mr.problem(w["d"], w["J"], **cap), stream=stream)
+    if RADAU_SCHEDULE is not None:
+        c.set_radau_schedule(RADAU_SCHEDULE)
+    return c
 
 
 def oracle_model(w):
@@ -425,10 +433,12 @@ def run_gpu(args, w):
         ach = rad_fl / (rad_ms * 1e-3) / 1e12
         kname = ("k_radau_team (Radau5, one 16-lane team per cell, FP64)" if w.get("model") == "network"
                  else "k_radau_team (Radau5, one warp per cell, numerical Jacobian, FP64)"
-                 if w.get("model") == "ionic" else "k_radau_pool (Radau5, phase-sorted cell pool, FP64)")
+                 if w.get("model") == "ionic" else "k_radau_pool (Radau5, phase-sorted cell pool, FP64)"
+                 if RADAU_SCHEDULE == 1 else "k_radau (Radau5, one thread per cell, FP64)")
         roof = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": fp64_tf,
                 "unit": "TFLOP/s", "frac": ach / fp64_tf,
-                "traffic": profiled_traffic("radau5.cu", "k_radau_pool_bz2d_J10.md")
+                "traffic": profiled_traffic("radau5.cu", "k_radau_pool_bz2d_J10.md" if RADAU_SCHEDULE == 1
+                                            else "k_radau_bz2d_J10.md")
                 if args.workload == DEFAULT else None,
                 "peak_source": "measured FP64 FMA rate of this GPU (library probe, 2 flop/FMA)",
                 "launches": rad_n, "ms_per_launch": rad_ms / max(rad_n, 1)}
@@ -565,7 +575,8 @@ def run_gpu(args, w):
             "config": {"workload": args.workload, "desc": w["desc"],
                        "l2": "flushed between timed steps (256 MB write)",
                        "leaves_last_step": st["leaves"], "compression_ratio": st["compression_ratio"],
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "radau_schedule": "pool" if RADAU_SCHEDULE == 1 else "thread"},
             "roofline": roof, "roofline_rock4": roof_rock, "roofline_adapt": roof_adapt, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "mixed": mixed, "hbm_point": hbm_point, "extras": extras,
             "operator_forms": forms,
@@ -1004,7 +1015,13 @@ def main():
     ap.add_argument("--instances", type=int, default=0,
                     help="batched workload: the first N of its seeded instances (profiling captures of a "
                          "smaller case); the line's config records it")
+    ap.add_argument("--radau-schedule", choices=("pool", "thread"), default=None,
+                    help="Radau5 schedule of single-context BZ and NAGUMO workloads (default: the library's, "
+                         "one thread per cell); both give bit-identical results")
     args = ap.parse_args()
+    if args.radau_schedule is not None:
+        global RADAU_SCHEDULE
+        RADAU_SCHEDULE = 1 if args.radau_schedule == "pool" else 0
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.workload in BATCH:

@@ -214,7 +214,8 @@ mr_status react_radau5(mr_ctx *ctx, double dt, double rtol, double atol);
  *                    Newton iteration; error estimate and step control) for
  *                    up to 32 cells that are in that phase.
  * Both run the same operations per cell in the same order, so results and
- * complexity counts are bit-identical.  New contexts use MR_RADAU_POOL.
+ * complexity counts are bit-identical.  New contexts use MR_RADAU_THREAD,
+ * the faster of the two on the measured workloads.
  * MR_EINVAL for another value. */
 mr_status mr_set_radau_schedule(mr_ctx *ctx, int schedule);
 
@@ -298,14 +299,13 @@ typedef struct {
  * per millisecond (Radau5: FP64 operations as in mr_stats; ROCK4: sweep
  * bytes), and the fastest is kept.  On by default.
  *   mr_batch_set_autotune  on = 1 restarts the trials, on = 0 fixes the
- *                          default shapes (the pooled Radau5 schedule,
- *                          finest first; 2 blocks per SM); MR_EINVAL
- *                          otherwise
+ *                          default shapes (128 threads, finest first; 2
+ *                          blocks per SM); MR_EINVAL otherwise
  *   mr_batch_tuning        the trial table: one entry per candidate (the
- *                          six Radau5 shapes: the pooled schedule in both
- *                          queue orders, the thread schedule with 128 or 64
- *                          threads per block in both; then the two ROCK4
- *                          shapes);
+ *                          six Radau5 shapes: the thread schedule with
+ *                          128 or 64 threads per block, then the pooled
+ *                          schedule, each in both queue orders; then the
+ *                          two ROCK4 shapes);
  *                          *n gets the number of entries, MR_ENOMEM if cap
  *                          is smaller
  */

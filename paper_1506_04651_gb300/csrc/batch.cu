@@ -142,16 +142,16 @@ struct mr_batch {
   mrg::Pool* pool = nullptr;
   mrg::BatchReactScratch scratch;
   mrg::BatchRockScratch rscratch;
-  // the joint Radau5 launch: the pooled schedule, or the thread schedule
-  // with 128 or 64 threads per block, each with the finest levels first or
+  // the joint Radau5 launch: the thread schedule with 128 or 64 threads
+  // per block, or the pooled schedule, each with the finest levels first or
   // in leaf order (the default first); the joint ROCK4 launch: 2 or 1 blocks
   // per SM
-  mrg::Tuner tune_react{{{128, 1, MR_RADAU_POOL},
-                         {128, 0, MR_RADAU_POOL},
-                         {128, 1, MR_RADAU_THREAD},
+  mrg::Tuner tune_react{{{128, 1, MR_RADAU_THREAD},
                          {64, 1, MR_RADAU_THREAD},
                          {128, 0, MR_RADAU_THREAD},
-                         {64, 0, MR_RADAU_THREAD}}};
+                         {64, 0, MR_RADAU_THREAD},
+                         {128, 1, MR_RADAU_POOL},
+                         {128, 0, MR_RADAU_POOL}}};
   mrg::Tuner tune_diffuse{{{2, 0}, {1, 0}}};
   mr_batch_stats stats;
   const char* last_error = "";

@@ -176,7 +176,7 @@ struct mr_ctx {
   cudaEvent_t ev[8];
   cudaEvent_t tev[2 * 256];           // per-launch timing pairs of the ROCK4 sweeps
   mr_stats stats;
-  int radau_schedule = MR_RADAU_POOL;  // Radau5 schedule of BZ and NAGUMO contexts
+  int radau_schedule = MR_RADAU_THREAD;  // Radau5 schedule of BZ and NAGUMO contexts
   void* radau_pool = nullptr;          // slot data of the pooled Radau5 kernel (lazy)
   size_t radau_pool_bytes = 0;
   int64_t launches = 0;

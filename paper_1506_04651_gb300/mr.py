@@ -245,7 +245,7 @@ class Context:
         return self._check(lib().react_radau5(self.h, dt, rtol, atol), "react_radau5")
 
     def set_radau_schedule(self, schedule):
-        """MR_RADAU_POOL (the default) or MR_RADAU_THREAD; bit-identical results."""
+        """MR_RADAU_THREAD (the default) or MR_RADAU_POOL; bit-identical results."""
         return self._check(lib().mr_set_radau_schedule(self.h, schedule), "mr_set_radau_schedule")
 
     def diffuse(self, dt, tol=1e-6):

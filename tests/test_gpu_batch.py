@@ -178,8 +178,8 @@ def test_full_batch_config_one_step(mr):
 
 def test_autotuner_changes_no_result(mr):
     """The batch's autotuner tries its candidate launch shapes on the first
-    launches (joint Radau5: the pooled schedule, or the thread schedule with
-    128 or 64 threads per block, each with the finest levels first or in leaf
+    launches (joint Radau5: the thread schedule with 128 or 64 threads per
+    block, or the pooled schedule, each with the finest levels first or in leaf
     order; joint ROCK4: 2 or 1 blocks per SM).  None of them changes
     a result: after six steps every instance equals, bit for bit, the same
     batch run with the default shapes fixed.  The trial table lists every

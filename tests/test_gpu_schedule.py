@@ -5,8 +5,8 @@ bit-identical: on the 2D BZ crossing fronts (several thousand stiff front
 cells among rest-state cells, in FP64 and in the mixed form), on a 3D
 sphere and on the NAGUMO front.  In a batch the autotuner tries both
 schedules and its test checks the results bit for bit against the default.
-The pooled kernel is the default; its agreement with the oracle is covered
-by every parity test that integrates reactions."""
+The thread kernel is the default and every parity test that integrates
+reactions compares it with the oracle; the pool matches it bit for bit."""
 import numpy as np
 import pytest
 
