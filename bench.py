@@ -833,7 +833,7 @@ def run_mixed(args, w, mr, torch, dev, stream, u0):
             "rel_l1_vs_fp64_path": err, "steps": nsteps,
             "grids_equal": bool(np.array_equal(kf, km)), "leaves_fp64": int(len(kf)), "leaves_mixed": int(len(km)),
             "rel_l1_on_common_leaves": err_common,
-            "form": "Radau5 Newton factorisations and solves in FP32; ROCK4 stage vectors in FP32; "
+            "form": "Radau5 Newton factorisations and solves, and the starting values and tolerance scales of each step attempt, in FP32; ROCK4 stage vectors in FP32; "
                     "Radau5 residuals, both error norms, step control, the state between sub-steps, "
                     "details and mass in FP64",
             "note": "no L2 flush between these steps; the FP64 path matches the oracle to 1e-9 per step",
@@ -965,7 +965,7 @@ def run_batch(args, b, print_line=True):
                  "rel_l1_vs_fp64_path_max_over_instances": max(errs),
                  "rel_l1_max_over_instances_with_equal_grids": max(errs_same) if errs_same else None,
                  "instances_with_different_grids": flipped,
-                 "form": "Radau5 Newton factorisations and solves in FP32; ROCK4 stage vectors in FP32; "
+                 "form": "Radau5 Newton factorisations and solves, and the starting values and tolerance scales of each step attempt, in FP32; ROCK4 stage vectors in FP32; "
                          "Radau5 residuals, both error norms, step control, the state between sub-steps, "
                          "details and mass in FP64"}
         Bm.close()

@@ -93,7 +93,9 @@ enum { MR_RADAU_THREAD = 0, MR_RADAU_POOL = 1 };
  *             diffused in windows of 16; windows whose coefficients are
  *             all zero cost nothing)
  *   precision MR_FP64, or MR_MIXED: Radau5 factorises and solves its Newton
- *             systems in FP32, and the ROCK4 stages and finishing procedure
+ *             systems in FP32 and forms the starting values and tolerance
+ *             scales of each step attempt in FP32, and the ROCK4 stages and
+ *             finishing procedure
  *             run on FP32 increments from the FP64 state (y_{n+1} - y_n and
  *             the stage differences; L y_n is applied in FP64 once per
  *             sub-step), so rounding is relative to the change a step makes

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <complex>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 #include <math.h>
 #include <string.h>
@@ -39,6 +40,9 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return fmaf(a, b, c); }
 // a0 b0 + a1 b1 + a2 b2, summed left to right
 __device__ __forceinline__ double dot3(double a0, double b0, double a1, double b1, double a2, double b2) {
+  return fma_rn(a2, b2, fma_rn(a1, b1, mul_rn(a0, b0)));
+}
+__device__ __forceinline__ float dot3(float a0, float b0, float a1, float b1, float a2, float b2) {
   return fma_rn(a2, b2, fma_rn(a1, b1, mul_rn(a0, b0)));
 }
 
@@ -285,7 +289,8 @@ struct RCell {
   LT E1[M * M], E2r[M * M], E2i[M * M];
   LT i1[M], i2r[M], i2i[M];
   int p1[M], p2[M];
-  double Z[3][M], W[3][M], cz[3][M], isc[M];
+  double Z[3][M], W[3][M], isc[M];
+  LT cz[3][M];  // stage increments of the last accepted step (for the starting values)
   double t, h, ih, ch, faccon, hacc, erracc, theta, dynold, hfac_fail, gi, ali, bei;
   int k, nsing;
   bool first, reject, have_cont, last, need_jac, jac_fresh;
@@ -374,6 +379,61 @@ __device__ __forceinline__ int r_factor(RCell<M, LT>& S, const RadauC& C, double
   return 0;
 }
 
+// Starting values of a step attempt: the cubic through (0,0), (c1,z1),
+// (c2,z2), (1,z3) of the last accepted step extrapolated to the new stage
+// times (zero before the first accepted step), their transform W = T^-1 Z,
+// the tolerance scales 1/(atol' + rtol' |y_i|) and the Newton-stopping factor
+// faccon^0.8.  With LT = double these are the method's FP64 operations; the
+// mixed form (LT = float) computes these initial guesses and scales in FP32
+// from the FP64 state, while the Newton residuals, the error estimate and the
+// step control stay FP64.  Shared by both Radau5 kernels.
+template <int M, typename LT>
+__device__ __forceinline__ void start_values(const RadauC& C, bool have_cont, double h, double ch, const LT (*cz)[M],
+                                             const double* y, double (*Z)[M], double (*W)[M], double* isc,
+                                             double& faccon) {
+  constexpr bool F32 = std::is_same<LT, float>::value;
+  LT Zl[3][M];
+  if (have_cont) {
+    const LT c1 = F32 ? (LT)C.c1f : (LT)C.c1, c2 = F32 ? (LT)C.c2f : (LT)C.c2;
+    const LT nd[4] = {LT(0), c1, c2, LT(1)};
+    const LT cs[3] = {c1, c2, LT(1)};
+    const LT r = F32 ? (LT)((float)h / (float)ch) : (LT)(h / ch);
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+      LT tau = fma_rn(cs[s], r, LT(1)), L[4];
+#pragma unroll
+      for (int a = 1; a < 4; a++) {
+        LT l = LT(1);
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+          if (b != a) l *= (tau - nd[b]) * (F32 ? (LT)C.idnf[a][b] : (LT)C.idn[a][b]);
+        L[a] = l;
+      }
+#pragma unroll
+      for (int i = 0; i < M; i++) Zl[s][i] = fma_rn(L[3], cz[2][i], fma_rn(L[2], cz[1][i], mul_rn(L[1], cz[0][i]))) - cz[2][i];
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < 3; s++)
+#pragma unroll
+      for (int i = 0; i < M; i++) Zl[s][i] = LT(0);
+  }
+#pragma unroll
+  for (int s = 0; s < 3; s++)
+#pragma unroll
+    for (int i = 0; i < M; i++) {
+      const LT t0 = F32 ? (LT)C.Tif[s * 3 + 0] : (LT)C.Ti[s * 3 + 0];
+      const LT t1 = F32 ? (LT)C.Tif[s * 3 + 1] : (LT)C.Ti[s * 3 + 1];
+      const LT t2 = F32 ? (LT)C.Tif[s * 3 + 2] : (LT)C.Ti[s * 3 + 2];
+      Z[s][i] = (double)Zl[s][i];
+      W[s][i] = (double)dot3(t0, Zl[0][i], t1, Zl[1][i], t2, Zl[2][i]);
+    }
+  const LT rt = F32 ? (LT)C.rtf : (LT)C.rt, at = F32 ? (LT)C.atf : (LT)C.at;
+#pragma unroll
+  for (int i = 0; i < M; i++) isc[i] = (double)(LT(1) / fma_rn(rt, (LT)fabs(y[i]), at));
+  faccon = F32 ? pow08_f32(fmax(faccon, RCtl::uround)) : pow08(fmax(faccon, RCtl::uround));
+}
+
 // Start of one step attempt: the step-count and step-size guards, starting
 // values (extrapolated from the last accepted step), the tolerance scales and
 // the Newton iteration's state.  0, or the failure status.
@@ -382,44 +442,10 @@ __device__ __forceinline__ int r_start(RCell<M, LT>& S, const RadauC& C, double 
   S.n.nstep++;
   if (S.n.nstep > 100000) return MR_ERADAU_MAXSTEPS;
   if (0.1 * S.h <= RCtl::uround * fmax(S.t, tend) || S.h <= 0.0) return MR_ERADAU_HMIN;
-  if (S.have_cont) {
-    // extrapolate the cubic through (0,0), (c1,z1), (c2,z2), (1,z3) of the
-    // last accepted step to the new stage times
-    const double nd[4] = {0.0, C.c1, C.c2, 1.0};
-    const double cs[3] = {C.c1, C.c2, 1.0};
-    const double r = S.h / S.ch;
-#pragma unroll
-    for (int s = 0; s < 3; s++) {
-      double tau = fma_rn(cs[s], r, 1.0), L[4];
-#pragma unroll
-      for (int a = 1; a < 4; a++) {
-        double l = 1.0;
-#pragma unroll
-        for (int b = 0; b < 4; b++)
-          if (b != a) l *= (tau - nd[b]) * C.idn[a][b];
-        L[a] = l;
-      }
-#pragma unroll
-      for (int i = 0; i < M; i++)
-        S.Z[s][i] = fma_rn(L[3], S.cz[2][i], fma_rn(L[2], S.cz[1][i], mul_rn(L[1], S.cz[0][i]))) - S.cz[2][i];
-    }
-  } else {
-#pragma unroll
-    for (int s = 0; s < 3; s++)
-#pragma unroll
-      for (int i = 0; i < M; i++) S.Z[s][i] = 0.0;
-  }
-#pragma unroll
-  for (int s = 0; s < 3; s++)
-#pragma unroll
-    for (int i = 0; i < M; i++)
-      S.W[s][i] = dot3(C.Ti[s * 3 + 0], S.Z[0][i], C.Ti[s * 3 + 1], S.Z[1][i], C.Ti[s * 3 + 2], S.Z[2][i]);
-#pragma unroll
-  for (int i = 0; i < M; i++) S.isc[i] = 1.0 / fma_rn(C.rt, fabs(S.y[i]), C.at);
+  start_values<M, LT>(C, S.have_cont, S.h, S.ch, S.cz, S.y, S.Z, S.W, S.isc, S.faccon);
   S.k = 0;
   S.dynold = 0.0;
   S.hfac_fail = 0.5;
-  S.faccon = pow08(fmax(S.faccon, RCtl::uround));
   S.theta = RCtl::thet;
   S.gi = C.gam * S.ih;
   S.ali = C.alp * S.ih;
@@ -584,7 +610,7 @@ __device__ __forceinline__ int r_estimate(RCell<Mdl::M, LT>& S, const RadauC& C,
 #pragma unroll
     for (int s = 0; s < 3; s++)
 #pragma unroll
-      for (int i = 0; i < M; i++) S.cz[s][i] = S.Z[s][i];
+      for (int i = 0; i < M; i++) S.cz[s][i] = (LT)S.Z[s][i];
     S.ch = S.h;
     S.have_cont = true;
     bool finite = true;
@@ -661,7 +687,8 @@ __global__ void __launch_bounds__(BS) k_radau(BatchCells<Mdl> B, RadauC C, int64
   LT E1[M * M], E2r[M * M], E2i[M * M];
   LT i1[M], i2r[M], i2i[M];
   int p1[M], p2[M];
-  double Z[3][M], W[3][M], cz[3][M], ch = 0.0;
+  double Z[3][M], W[3][M], ch = 0.0;
+  LT cz[3][M];
   double t = 0.0, h = tend, ih = 1.0 / tend;
   bool first = true, reject = false, have_cont = false, last = false;
   bool need_jac = true, jac_fresh = false;
@@ -776,43 +803,10 @@ __global__ void __launch_bounds__(BS) k_radau(BatchCells<Mdl> B, RadauC C, int64
         st = MR_ERADAU_HMIN;
         finish = true;
       } else {
-        if (have_cont) {
-          // extrapolate the cubic through (0,0), (c1,z1), (c2,z2), (1,z3) of
-          // the last accepted step to the new stage times
-          const double nd[4] = {0.0, C.c1, C.c2, 1.0};
-          const double cs[3] = {C.c1, C.c2, 1.0};
-          const double r = h / ch;
-#pragma unroll
-          for (int s = 0; s < 3; s++) {
-            double tau = fma_rn(cs[s], r, 1.0), L[4];
-#pragma unroll
-            for (int a = 1; a < 4; a++) {
-              double l = 1.0;
-#pragma unroll
-              for (int b = 0; b < 4; b++)
-                if (b != a) l *= (tau - nd[b]) * C.idn[a][b];
-              L[a] = l;
-            }
-#pragma unroll
-            for (int i = 0; i < M; i++) Z[s][i] = fma_rn(L[3], cz[2][i], fma_rn(L[2], cz[1][i], mul_rn(L[1], cz[0][i]))) - cz[2][i];
-          }
-        } else {
-#pragma unroll
-          for (int s = 0; s < 3; s++)
-#pragma unroll
-            for (int i = 0; i < M; i++) Z[s][i] = 0.0;
-        }
-#pragma unroll
-        for (int s = 0; s < 3; s++)
-#pragma unroll
-          for (int i = 0; i < M; i++)
-            W[s][i] = dot3(C.Ti[s * 3 + 0], Z[0][i], C.Ti[s * 3 + 1], Z[1][i], C.Ti[s * 3 + 2], Z[2][i]);
-#pragma unroll
-        for (int i = 0; i < M; i++) isc[i] = 1.0 / fma_rn(rt, fabs(y[i]), at);
+        start_values<M, LT>(C, have_cont, h, ch, cz, y, Z, W, isc, faccon);
         k = 0;
         dynold = 0.0;
         hfac_fail = 0.5;
-        faccon = pow08(fmax(faccon, uround));
         theta = thet;
         gi = C.gam * ih;
         ai_ = C.alp * ih;
@@ -964,7 +958,7 @@ __global__ void __launch_bounds__(BS) k_radau(BatchCells<Mdl> B, RadauC C, int64
 #pragma unroll
           for (int s = 0; s < 3; s++)
 #pragma unroll
-            for (int i = 0; i < M; i++) cz[s][i] = Z[s][i];
+            for (int i = 0; i < M; i++) cz[s][i] = (LT)Z[s][i];
           ch = h;
           have_cont = true;
           bool finite = true;
@@ -1083,12 +1077,12 @@ __device__ __forceinline__ int slot_task(int v) {
 // Structure-of-arrays slot data: field f of slot s at base[f * P + s].
 template <int M, typename LT>
 struct PoolLayout {
-  // doubles: y, f0, J, Z, W, cz, isc, 13 scalars
-  static constexpr int DY = 0, DF0 = M, DJ = 2 * M, DZ = 2 * M + M * M, DW = DZ + 3 * M, DCZ = DW + 3 * M,
-                       DISC = DCZ + 3 * M, DSC = DISC + M, ND = DSC + 13;
-  // LT: E1, E2r, E2i, i1, i2r, i2i
+  // doubles: y, f0, J, Z, W, isc, 13 scalars
+  static constexpr int DY = 0, DF0 = M, DJ = 2 * M, DZ = 2 * M + M * M, DW = DZ + 3 * M, DISC = DW + 3 * M,
+                       DSC = DISC + M, ND = DSC + 13;
+  // LT: E1, E2r, E2i, i1, i2r, i2i, cz
   static constexpr int LE1 = 0, LE2R = M * M, LE2I = 2 * M * M, LI1 = 3 * M * M, LI2R = LI1 + M, LI2I = LI2R + M,
-                       NL = LI2I + M;
+                       LCZ = LI2I + M, NL = LCZ + 3 * M;
   // int: p1, p2, k, nsing, flags, 7 counters, instance, cell (2 words)
   static constexpr int IP1 = 0, IP2 = M, IK = 2 * M, INS = IK + 1, IFL = IK + 2, ICN = IK + 3, IINST = ICN + 7,
                        ICELL = IINST + 1, NI = ICELL + 2;
@@ -1138,7 +1132,7 @@ __device__ __forceinline__ void pool_load(const PoolRef<M, LT>& R, int s, RCell<
     }
   if (g & G_CZ)
 #pragma unroll
-    for (int q = 0; q < 3 * M; q++) S.cz[q / M][q % M] = R.d(PL::DCZ + q, s);
+    for (int q = 0; q < 3 * M; q++) S.cz[q / M][q % M] = R.l(PL::LCZ + q, s);
   if (g & G_ISC)
 #pragma unroll
     for (int i = 0; i < M; i++) S.isc[i] = R.d(PL::DISC + i, s);
@@ -1220,7 +1214,7 @@ __device__ __forceinline__ void pool_store(const PoolRef<M, LT>& R, int s, const
     }
   if (g & G_CZ)
 #pragma unroll
-    for (int q = 0; q < 3 * M; q++) R.d(PL::DCZ + q, s) = S.cz[q / M][q % M];
+    for (int q = 0; q < 3 * M; q++) R.l(PL::LCZ + q, s) = S.cz[q / M][q % M];
   if (g & G_ISC)
 #pragma unroll
     for (int i = 0; i < M; i++) R.d(PL::DISC + i, s) = S.isc[i];
@@ -1623,6 +1617,12 @@ RadauC constants_from(const double* rc) {
     for (int b = 0; b < 4; b++) C.idn[a][b] = a == b ? 0.0 : 1.0 / (nd[a] - nd[b]);
   const int kmax = 7;
   for (int k = 0; k < 8; k++) C.fac[k] = std::min(0.9, 0.9 * (1 + 2 * kmax) / (double)(k + 2 * kmax));
+  C.c1f = (float)C.c1;
+  C.c2f = (float)C.c2;
+  for (int q = 0; q < 9; q++) C.Tif[q] = (float)C.Ti[q];
+  for (int a = 0; a < 4; a++)
+    for (int b = 0; b < 4; b++) C.idnf[a][b] = (float)C.idn[a][b];
+  C.rtf = C.atf = 0.0f;
   return C;
 }
 
@@ -1761,6 +1761,8 @@ mr_status react(mr_ctx* c, double dt, double rtol, double atol) {
   // tolerance transformation of the published method, evaluated once on the host
   C.rt = 0.1 * pow(rtol, 2.0 / 3.0);
   C.at = C.rt * (atol / rtol);
+  C.rtf = (float)C.rt;
+  C.atf = (float)C.at;
   C.fnewt = std::max(10.0 * 1e-16 / C.rt, std::min(0.03, sqrt(C.rt)));
   C.ifnewt = 1.0 / C.fnewt;
   if (c->prob.model == MR_MODEL_NETWORK) return react_network(c, C, dt);
@@ -1919,6 +1921,8 @@ mr_status react_batch(mr_ctx* const* cs, int n, double dt, double rtol, double a
   RadauC C = constants_from(cs[0]->rc);
   C.rt = 0.1 * pow(rtol, 2.0 / 3.0);
   C.at = C.rt * (atol / rtol);
+  C.rtf = (float)C.rt;
+  C.atf = (float)C.at;
   C.fnewt = std::max(10.0 * 1e-16 / C.rt, std::min(0.03, sqrt(C.rt)));
   C.ifnewt = 1.0 / C.fnewt;
   if (cudaMemsetAsync(S.dc, 0, sizeof(DevCounters), stream) != cudaSuccess ||
@@ -2003,6 +2007,8 @@ mr_status react_noalloc(int model, const double* params, int nparams, double* u,
   RadauC C = constants_from(rc);
   C.rt = 0.1 * pow(rtol, 2.0 / 3.0);
   C.at = C.rt * (atol / rtol);
+  C.rtf = (float)C.rt;
+  C.atf = (float)C.at;
   C.fnewt = std::max(10.0 * 1e-16 / C.rt, std::min(0.03, sqrt(C.rt)));
   C.ifnewt = 1.0 / C.fnewt;
   if (cudaMemsetAsync(dc, 0, sizeof(DevCounters), stream) != cudaSuccess) return MR_ECUDA;

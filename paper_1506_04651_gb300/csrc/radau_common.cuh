@@ -16,6 +16,9 @@ struct RadauC {
   double rt, at, fnewt;  // transformed tolerances and Newton tolerance (per call)
   double ifnewt;         // 1 / fnewt
   double fac[8];       // min(0.9, 0.9 (1 + 2 kmax)/(k + 2 kmax)), k Newton iterations
+  // FP32 copies for the mixed form's starting values and tolerance scales
+  float c1f, c2f, Tif[9], idnf[4][4];
+  float rtf, atf;  // set with rt, at
 };
 
 struct CellCount {
@@ -41,6 +44,10 @@ __device__ inline double pow08(double x) {
   }
   return y;
 }
+
+// the mixed form's x^0.8: the FP32 estimate alone (the factor only enters
+// the comparison with the Newton tolerance)
+__device__ inline double pow08_f32(double x) { return (double)exp2f(__fmul_rn(0.8f, log2f((float)x))); }
 
 // kernel-side constants from radau_constants' array (tolerances unset)
 RadauC constants_from(const double* rc);
