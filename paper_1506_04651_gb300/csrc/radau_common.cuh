@@ -31,18 +31,19 @@ __device__ inline double clampd(double x, double lo, double hi) { return fmin(fm
 __device__ inline double root4(double x) { return sqrt(sqrt(x)); }
 
 // x^0.8 (x in [1e-16, 100]) for the Newton-stopping factor of each step
-// attempt: an FP32 estimate refined by two FP64 Newton steps on y^5 = x^4,
-// within a few ulps of pow at a fraction of its FP64 instructions (the factor
-// only enters the comparison with the Newton tolerance)
+// attempt, without FP64 division: x^0.8 = x z with z = x^(-1/5), from an FP32
+// estimate refined by two Newton steps on z^-5 = x written as
+// z <- z (1 + (1 - x z^5) / 5) (quadratic convergence); within a few ulps of
+// pow (the factor only enters the comparison with the Newton tolerance)
 __device__ inline double pow08(double x) {
-  double y = (double)exp2f(__fmul_rn(0.8f, log2f((float)x)));
-  const double x2 = x * x, x4 = x2 * x2;
+  double z = (double)exp2f(__fmul_rn(-0.2f, log2f((float)x)));
 #pragma unroll
   for (int q = 0; q < 2; q++) {
-    const double y2 = y * y;
-    y = fma(x4 / (y2 * y2) - y, 0.2, y);
+    const double z2 = z * z, z5 = z2 * z2 * z;
+    const double e = fma(-x, z5, 1.0);
+    z = fma(z * e, 0.2, z);
   }
-  return y;
+  return x * z;
 }
 
 // the mixed form's x^0.8: the FP32 estimate alone (the factor only enters
@@ -74,7 +75,10 @@ RadauC constants_from(const double* rc);
 //              1 + 3 (2 + 27 + 6M) = 88 + 18M
 //   accept     error estimate 5 + 13M + solve_real(M), step-size factor 4,
 //              accepted-step control, update and time 11 + M
-// A launch's work is taken as the lower bound
+// Where the source trades divisions for multiplications (the tolerance
+// scales as one reciprocal of their product, the contraction monitor with
+// one division, faccon^0.8 without division) the table keeps the smaller
+// division forms' counts.  A launch's work is taken as the lower bound
 //   rhs nfev + jac njac + dec ndec + newton nnewton + monitor (nnewton - nstep)
 //   + attempt nstep + extrap max(0, nstep - ncells - nreject) + accept naccept
 // (an attempt extrapolates unless it precedes its cell's first accepted
