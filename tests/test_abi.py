@@ -81,3 +81,16 @@ def test_noalloc_maximum_rejected_before_gpu_work(native):
     buf = (C.c_double * 4)()
     assert f(1, params, 4, C.addressof(buf), mx + 1, mx + 1, 5e-4, 1e-6, 1e-6, None, None) == -1
     assert f(1, params, 4, C.addressof(buf), -1, 4, 5e-4, 1e-6, 1e-6, None, None) == -1
+
+
+def test_radau_schedule_setter_rejects_bad_arguments(native):
+    """mr_set_radau_schedule accepts only MR_RADAU_THREAD and MR_RADAU_POOL,
+    and a context; anything else is MR_EINVAL with no device work (no
+    context is created here)."""
+    src = open(os.path.join(ROOT, "include", "mr.h")).read()
+    vals = dict(re.findall(r"(MR_RADAU_(?:THREAD|POOL)) = (\d+)", src))
+    assert int(vals["MR_RADAU_THREAD"]) == native.MR_RADAU_THREAD == 0
+    assert int(vals["MR_RADAU_POOL"]) == native.MR_RADAU_POOL == 1
+    f = native.lib().mr_set_radau_schedule
+    for sched in (0, 1, 2, -1):
+        assert f(None, sched) == -1
