@@ -313,7 +313,7 @@ def radau_work(model, m):
     sol_real = m + 2 * m * (m - 1)
     return {"rhs": 13 if model == "bz" else 4, "jac": 10 if model == "bz" else 5,
             "dec": 6 + 2 * m + lu_real + lu_cplx, "newton": 62 * m + 10 * m * (m - 1) + 3, "monitor": 6,
-            "attempt": 19 + 18 * m, "extrap": 88 + 18 * m, "accept": (5 + 13 * m + sol_real) + 4 + (11 + m)}
+            "attempt": 19 + 18 * m, "extrap": 55 + 18 * m, "accept": (5 + 13 * m + sol_real) + 4 + (11 + m)}
 
 
 def radau_flops(work, cnt):

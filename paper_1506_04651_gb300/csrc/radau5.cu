@@ -402,7 +402,8 @@ __device__ __forceinline__ int r_factor(RCell<M, LT>& S, const RadauC& C, double
 
 // Starting values of a step attempt: the cubic through (0,0), (c1,z1),
 // (c2,z2), (1,z3) of the last accepted step extrapolated to the new stage
-// times (zero before the first accepted step), their transform W = T^-1 Z,
+// times (zero before the first accepted step; its Lagrange weights are
+// cubics in the step ratio whose coefficients the host computes), their transform W = T^-1 Z,
 // the tolerance scales 1/(atol' + rtol' |y_i|) and the Newton-stopping factor
 // faccon^0.8.  With LT = double these are the method's FP64 operations; the
 // mixed form (LT = float) computes these initial guesses and scales in FP32
@@ -415,20 +416,17 @@ __device__ __forceinline__ void start_values(const RadauC& C, bool have_cont, do
   constexpr bool F32 = std::is_same<LT, float>::value;
   LT Zl[3][M];
   if (have_cont) {
-    const LT c1 = F32 ? (LT)C.c1f : (LT)C.c1, c2 = F32 ? (LT)C.c2f : (LT)C.c2;
-    const LT nd[4] = {LT(0), c1, c2, LT(1)};
-    const LT cs[3] = {c1, c2, LT(1)};
     const LT r = F32 ? (LT)((float)h / (float)ch) : (LT)(h / ch);
 #pragma unroll
     for (int s = 0; s < 3; s++) {
-      LT tau = fma_rn(cs[s], r, LT(1)), L[4];
+      LT L[4];
 #pragma unroll
       for (int a = 1; a < 4; a++) {
-        LT l = LT(1);
-#pragma unroll
-        for (int b = 0; b < 4; b++)
-          if (b != a) l *= (tau - nd[b]) * (F32 ? (LT)C.idnf[a][b] : (LT)C.idn[a][b]);
-        L[a] = l;
+        const LT c0 = F32 ? (LT)C.Lcf[s][a - 1][0] : (LT)C.Lc[s][a - 1][0];
+        const LT c1 = F32 ? (LT)C.Lcf[s][a - 1][1] : (LT)C.Lc[s][a - 1][1];
+        const LT c2 = F32 ? (LT)C.Lcf[s][a - 1][2] : (LT)C.Lc[s][a - 1][2];
+        const LT c3 = F32 ? (LT)C.Lcf[s][a - 1][3] : (LT)C.Lc[s][a - 1][3];
+        L[a] = fma_rn(fma_rn(fma_rn(c3, r, c2), r, c1), r, c0);
       }
 #pragma unroll
       for (int i = 0; i < M; i++) Zl[s][i] = fma_rn(L[3], cz[2][i], fma_rn(L[2], cz[1][i], mul_rn(L[1], cz[0][i]))) - cz[2][i];
@@ -1593,7 +1591,7 @@ RadauWork radau_work(int model, int M) {
   w.newton = 62 * m + 10 * m * (m - 1) + 3;
   w.monitor = 6;
   w.attempt = 19 + 18 * m;
-  w.extrap = 88 + 18 * m;
+  w.extrap = 55 + 18 * m;
   w.accept = (5 + 13 * m + sol_real) + 4 + (11 + m);
   return w;
 }
@@ -1657,6 +1655,24 @@ RadauC constants_from(const double* rc) {
     for (int b = 0; b < 4; b++) C.idn[a][b] = a == b ? 0.0 : 1.0 / (nd[a] - nd[b]);
   const int kmax = 7;
   for (int k = 0; k < 8; k++) C.fac[k] = std::min(0.9, 0.9 * (1 + 2 * kmax) / (double)(k + 2 * kmax));
+  // Lagrange weights on the nodes (0, c1, c2, 1) at tau = 1 + cs r expanded
+  // in r: the product over b != a of (1 - nd_b) idn_ab + cs idn_ab r
+  {
+    const double cs[3] = {C.c1, C.c2, 1.0};
+    for (int st = 0; st < 3; st++)
+      for (int a = 1; a < 4; a++) {
+        double poly[4] = {1.0, 0.0, 0.0, 0.0};
+        for (int b = 0; b < 4; b++) {
+          if (b == a) continue;
+          const double u = (1.0 - nd[b]) * C.idn[a][b], v = cs[st] * C.idn[a][b];
+          for (int d = 3; d >= 0; d--) poly[d] = poly[d] * u + (d > 0 ? poly[d - 1] * v : 0.0);
+        }
+        for (int d = 0; d < 4; d++) {
+          C.Lc[st][a - 1][d] = poly[d];
+          C.Lcf[st][a - 1][d] = (float)poly[d];
+        }
+      }
+  }
   C.c1f = (float)C.c1;
   C.c2f = (float)C.c2;
   for (int q = 0; q < 9; q++) C.Tif[q] = (float)C.Ti[q];

@@ -16,8 +16,11 @@ struct RadauC {
   double rt, at, fnewt;  // transformed tolerances and Newton tolerance (per call)
   double ifnewt;         // 1 / fnewt
   double fac[8];       // min(0.9, 0.9 (1 + 2 kmax)/(k + 2 kmax)), k Newton iterations
+  // starting values: the Lagrange weight of node a (1..3) at stage time
+  // 1 + c_s r as a cubic in the step ratio r, Lc[s][a-1][0..3] (ascending)
+  double Lc[3][3][4];
   // FP32 copies for the mixed form's starting values and tolerance scales
-  float c1f, c2f, Tif[9], idnf[4][4];
+  float c1f, c2f, Tif[9], idnf[4][4], Lcf[3][3][4];
   float rtf, atf;  // set with rt, at
 };
 
@@ -72,7 +75,9 @@ RadauC constants_from(const double* rc);
 //   attempt    every step attempt: step-size floor 2, W = T^-1 Z 15M, scales
 //              3M, faccon^0.8 14, shifted eigenvalues 3 = 19 + 18M
 //   extrap     starting values extrapolated from the last accepted step:
-//              1 + 3 (2 + 27 + 6M) = 88 + 18M
+//              the step ratio 1, nine Lagrange weights as cubics in it
+//              (Horner, 3 fused multiply-adds = 6 each) and the stage values
+//              6M per stage: 1 + 3 (18 + 6M) = 55 + 18M
 //   accept     error estimate 5 + 13M + solve_real(M), step-size factor 4,
 //              accepted-step control, update and time 11 + M
 // Where the source trades divisions for multiplications (the tolerance
