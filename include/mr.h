@@ -203,7 +203,10 @@ mr_status mr_adapt(mr_ctx *ctx, double eta);
  * failures MR_ERADAU_HMIN (step size underflow), MR_ERADAU_MAXSTEPS (over
  * 100000 attempts), MR_ERADAU_SINGULAR (five singular Newton matrices in a
  * row), MR_ENONFINITE (a non-finite state); MR_ESTATE for a network model
- * whose reactions are not set. */
+ * whose reactions are not set.  With the MR_RADAU_POOL schedule also
+ * MR_ENOMEM if its slot buffer (about 64 MB, allocated on the first pooled
+ * launch of the context) cannot be allocated, and MR_ETIMEOUT if one of its
+ * bounded waits runs out. */
 mr_status react_radau5(mr_ctx *ctx, double dt, double rtol, double atol);
 
 /* Schedule of the Radau5 launches of BZ and NAGUMO contexts (the network
