@@ -1096,12 +1096,6 @@ __global__ void __launch_bounds__(BS) k_radau(BatchCells<Mdl> B, RadauC C, int64
 // warp queues, loads or stores (measured 61% busy against 84% for the
 // thread-per-cell kernel).  Writes and reads of a slot's data are ordered by
 // block-scope fences around the atomic hand-over of its queue entry.
-//
-// On the measured BZ workloads the warps are fuller (24 against 19 lanes) but
-// the FP64 pipe idles more (69% against 84% busy) while warps load, store and
-// queue, and the launch is 13% longer, so this schedule is an option
-// (mr_set_radau_schedule, a batch-tuner candidate), not the default.
-
 // next phase of a slot (SL_BUSY: none, the slot is held by a warp)
 enum : int {
   SL_DEAD = 0,     // no cell, and the work queue is empty
