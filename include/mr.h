@@ -389,6 +389,19 @@ mr_status mr_operator_forms(mr_ctx *ctx, int reps, double *ms_compact, double *m
 mr_status mr_rock4_coefficients(int s, double *mu, double *nu, double *kap, double *w,
                                 double *errc, double *ell);
 
+/* The per-event FP64 operation counts of the one-thread-per-cell Radau5
+ * kernel (App. A counts right-hand sides and Jacobians; the other events
+ * follow the method's steps, Hairer and Wanner Sec. IV.8) from which
+ * mr_stats.radau_alg_flops is formed, for model MR_MODEL_BZ or
+ * MR_MODEL_NAGUMO with m species: out[0..7] = right-hand side, Jacobian,
+ * factorisations, Newton iteration without its right-hand sides,
+ * contraction monitor, step attempt, extrapolated starting values,
+ * accepted step.  A launch's work is rhs fev + jac njac + dec ndec + newton
+ * nnewton + monitor (nnewton - steps) + attempt steps + extrap max(0, steps -
+ * cells - reject) + accept naccept.  Host only; MR_EINVAL for another model
+ * or a null out. */
+mr_status mr_radau_work(int model, int m, double *out);
+
 /*
  * Reaction of a plain array of cells that allocates nothing.  The paper has
  * no counterpart; this entry point is for callers that cannot allocate device

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "mr_internal.cuh"
+#include "radau_common.cuh"
 
 namespace mrg {
 
@@ -590,6 +591,14 @@ mr_status mr_operator_forms(mr_ctx* c, int reps, double* ms_compact, double* ms_
 mr_status mr_fp64_fma_rate(double* tflops, double* mhz) {
   if (!tflops) return MR_EINVAL;
   return fp64_probe(tflops, mhz);
+}
+
+mr_status mr_radau_work(int model, int m, double* out) {
+  if (!out || (model != MR_MODEL_BZ && model != MR_MODEL_NAGUMO) || m < 1) return MR_EINVAL;
+  const RadauWork w = radau_work(model, m);
+  const double v[8] = {w.rhs, w.jac, w.dec, w.newton, w.monitor, w.attempt, w.extrap, w.accept};
+  for (int q = 0; q < 8; q++) out[q] = v[q];
+  return MR_OK;
 }
 
 mr_status mr_rock4_coefficients(int s, double* mu, double* nu, double* kap, double* w, double* errc, double* ell) {

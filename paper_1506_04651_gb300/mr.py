@@ -88,6 +88,7 @@ def lib():
             "mr_operator_forms": [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), i64p,
                                   C.POINTER(C.c_double)],
             "mr_rock4_coefficients": [C.c_int, dp, dp, dp, dp, dp, C.POINTER(C.c_double)],
+            "mr_radau_work": [C.c_int, C.c_int, dp],
             "mr_last_error": [vp, C.c_char_p, C.c_size_t],
             "mr_fp64_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
             "mr_save": [vp, C.c_char_p],
@@ -314,6 +315,16 @@ def rock4_coefficients(s):
     if rc:
         raise MRError(rc, "mr_rock4_coefficients")
     return dict(mu=mu, nu=nu, kap=kap, w=w, errc=errc, ell=ell.value)
+
+
+def radau_work(model, m):
+    """The library's per-event FP64 operation counts of the Radau5 kernel
+    (rhs, jac, dec, newton, monitor, attempt, extrap, accept)."""
+    out = np.zeros(8)
+    rc = lib().mr_radau_work(model, m, C.c_void_p(out.ctypes.data))
+    if rc:
+        raise MRError(rc, "mr_radau_work")
+    return dict(zip(("rhs", "jac", "dec", "newton", "monitor", "attempt", "extrap", "accept"), out.tolist()))
 
 
 def status_str(code):

@@ -94,3 +94,22 @@ def test_radau_schedule_setter_rejects_bad_arguments(native):
     f = native.lib().mr_set_radau_schedule
     for sched in (0, 1, 2, -1):
         assert f(None, sched) == -1
+
+
+@pytest.mark.parametrize("model,name,m", [(1, "bz", 3), (2, "nagumo", 1)])
+def test_radau_work_table_matches_bench(native, model, name, m):
+    """The per-event FP64 operation counts the library forms
+    mr_stats.radau_alg_flops from, and the copy bench.py reports beside the
+    counters (work_per_event), are the same numbers, so a reader can
+    recompute the roofline's achieved rate from either."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    lib_w = native.radau_work(model, m)
+    bench_w = bench.radau_work(name, m)
+    assert set(lib_w) == set(bench_w)
+    for k in lib_w:
+        assert lib_w[k] == bench_w[k], k
+    with pytest.raises(native.MRError):
+        native.radau_work(3, 16)  # the network model has team kernels, not this table
